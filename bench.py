@@ -1,0 +1,343 @@
+"""Benchmark: Wiener-filter solves per second on 1024 x 1024 maps with
+three-part noise (white + isotropic 1/f + horizontal stripes, 5% disc mask),
+to a relative residual of 1e-5, and the HBM roofline fraction of the
+dominant kernel.
+
+One step = one whole solve through the C ABI (wf_solve): setup of the
+problem, the messenger iteration with its cooling schedule and residual
+checkpoints until the stop test passes, and the export of s.  Inputs are
+seeded synthetic maps (see paper_1704_00865_gb300.synth) resident in HBM
+before the timed region; L2 is flushed (a 512 MiB write) between steps,
+outside the per-step CUDA events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload.  Under torchrun (N > 1) every rank solves its
+own maps (replicas, no collective); rank 0 prints the JSON line.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+# ---------------------------------------------------------------- workload
+N = 1024
+SEED = 1000
+TOL_RHO = 1e-6          # stop test on ||Delta d_u||/||d_u|| and ||g_m||/||g||
+SCHED_LAM_HI = 1e4      # fixed cooling schedule: geometric levels to 1
+SCHED_LEVELS = 20
+SCHED_ITERS = 50
+RESIDUAL_EVERY = 10
+CHECK_EVERY = 16
+MAX_ITERS = 400000
+# iterations per solve of this seeded workload (the count wf_solve reports;
+# the reference arm scales its per-iteration time by it)
+ITERS_PER_SOLVE = None
+
+METRIC = "WF solves/sec to rel. residual 1e-5 at 1024^2 3-noise; % HBM roofline"
+UNIT = "solves/s"
+# algorithmic bytes per pixel of one launch (fields in FP32)
+ROW_BYTES_PER_PX = 28   # read d+Nbar (8), d_RF, t_RF, d_2DF (12); write d_RF, t_RF (8)
+COL_BYTES_PER_PX = 20   # read t_RF, t_2DF, (C, P1f) (12); write t_2DF, d_2DF (8)
+
+
+def workload_config():
+    return {"workload": f"multi-messenger WF {N}x{N}, white(log-normal)+1/f(k_knee=20)+stripes(k_knee_x=20), "
+                        f"5% disc mask, seed {SEED}",
+            "map": [N, N], "noise_parts": ["white+mask", "1/f", "stripes"],
+            "schedule": {"kind": "fixed", "lam_hi": SCHED_LAM_HI, "levels": SCHED_LEVELS,
+                         "iters_per_level": SCHED_ITERS, "then": "lambda=1 to tol"},
+            "tol_rho": TOL_RHO, "residual_every": RESIDUAL_EVERY,
+            "l2": "flushed between steps (512 MiB write), outside the timed events"}
+
+
+def schedule_levels():
+    lv = [float(SCHED_LAM_HI ** ((SCHED_LEVELS - 1 - j) / (SCHED_LEVELS - 1))) for j in range(SCHED_LEVELS)]
+    return lv, [SCHED_ITERS] * SCHED_LEVELS
+
+
+def problem():
+    from paper_1704_00865_gb300 import synth
+    return synth.cfg1_problem(SEED, N)
+
+
+def _src_sha():
+    h = hashlib.sha256()
+    cdir = os.path.join(ROOT, "paper_1704_00865_gb300", "csrc")
+    for f in sorted(os.listdir(cdir)):
+        h.update(open(os.path.join(cdir, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel):
+    """ncu DRAM bytes per launch for `kernel`, if the committed capture was
+    taken on the current kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        d = json.load(open(p))
+    except Exception:
+        return None
+    e = d.get(kernel)
+    if not e or e.get("source_sha") != _src_sha():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _oracle_iter_time(prob, iters, workers=1):
+    import oracle as O
+    O.set_workers(workers)
+    lv, its = schedule_levels()
+    P = O.build_parts(prob)
+    ch = O.Chain(P)
+    ch.sweep(lv[0])  # warm the FFT plans
+    t = time.perf_counter()
+    for _ in range(iters):
+        ch.sweep(lv[0])
+    return (time.perf_counter() - t) / iters
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    prob = problem()
+    per_step_iters = 4
+    for _ in range(args.warmup):
+        _oracle_iter_time(prob, 1)
+    times = [_oracle_iter_time(prob, per_step_iters) for _ in range(args.steps)]
+    t_iter = statistics.mean(times)
+    ips = ITERS_PER_SOLVE
+    value = (1.0 / (t_iter * ips)) if ips else None
+    sample = (f"{per_step_iters} oracle sweeps of the {N}^2 three-part solve per step, {args.steps} steps; "
+              f"solves/s = 1/(t_iter x {ips} iterations per solve of this seeded workload)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_iter * (ips or 0) * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             "s_per_iter": t_iter},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_1704_00865_gb300 import build, wf
+    build.build()
+    wf.load()
+
+    prob = problem()
+    dev = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    host = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    inputs_d = [dev(a) for a in (prob.d, prob.pixel_var, prob.mask, prob.C, prob.P1f, prob.Pst, prob.stripe_amp2)]
+    inputs_h = [host(a) for a in (prob.d, prob.pixel_var, prob.mask, prob.C, prob.P1f, prob.Pst, prob.stripe_amp2)]
+    h2d = sum(t.numel() * t.element_size() for t in inputs_h if t is not None)
+    out_d = torch.empty(N, N, device="cuda")
+    out_h = torch.empty(N, N).pin_memory()
+    d2h = out_h.numel() * out_h.element_size()
+    flush = torch.empty(512 * 1024 * 1024 // 4, device="cuda")
+
+    params = wf.make_params(residual_every=RESIDUAL_EVERY, max_iters=MAX_ITERS, check_every=CHECK_EVERY)
+    plan = wf.Plan(N, N, wf.parts_of(prob), params)
+    lv, its = schedule_levels()
+    sched = wf.make_schedule("fixed", lv, its)
+    stream = torch.cuda.current_stream()
+
+    def step(inp, out):
+        return plan.solve(*inp, sched, TOL_RHO, out=out)[1]
+
+    for _ in range(max(args.warmup, 0)):
+        st = step(inputs_d, out_d)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    launches0 = plan.launch_count()
+    ms, stats = [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = step(inputs_d, out_d)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        stats.append(st)
+    torch.cuda.synchronize()
+    launches = plan.launch_count() - launches0
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    t_total = sum(ms) / 1e3
+    if ws > 1:
+        tt = torch.tensor([t_total], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_total = float(tt.item())
+    value = ws * args.steps / t_total
+
+    # end to end: host (pinned) inputs and output through the same call
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step(inputs_h, out_h)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    e2e_value = ws * args.steps / (sum(e2e_ms) / 1e3)
+
+    # dominant kernels, timed live with CUDA events on the plan's stream
+    plan.set_problem(*inputs_d)
+    plan.iterate(1.0, 20)
+    us_row, us_col = plan.time_passes(1.0, 200)
+    peaks, peak_kind = _peaks()
+    row_bytes = ROW_BYTES_PER_PX * N * N
+    col_bytes = COL_BYTES_PER_PX * N * N
+    row_gbs = row_bytes / (us_row * 1e-6) / 1e9
+    col_gbs = col_bytes / (us_col * 1e-6) / 1e9
+    dom = ("row_pass", row_gbs, row_bytes, us_row) if us_row >= us_col else ("col_pass", col_gbs, col_bytes, us_col)
+    peak = float(peaks["hbm_gbs"])
+    roof = {"bound": "hbm", "kernel": dom[0], "achieved": round(dom[1], 1), "peak": peak, "unit": "GB/s",
+            "frac": round(dom[1] / peak, 4), "traffic": _traffic(dom[0]),
+            "algorithmic_bytes_per_launch": dom[2], "us_per_launch": round(dom[3], 3),
+            "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs)",
+            "other": {"row_pass_gbs": round(row_gbs, 1), "col_pass_gbs": round(col_gbs, 1),
+                      "us_row": round(us_row, 3), "us_col": round(us_col, 3)}}
+
+    iters = [s["iters"] for s in stats]
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        t_iter = _oracle_iter_time(prob, 3)
+        ips = statistics.median(iters)
+        cpu = {"value": 1.0 / (t_iter * ips), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"3 FP64 oracle sweeps of this {N}^2 solve (numpy/scipy, 1 thread), "
+                         f"{t_iter:.3f} s/iteration, scaled by the {ips:.0f} iterations per solve measured here",
+               "s_per_iter": t_iter}
+    cfg = workload_config()
+    cfg.update({"iters_per_solve": iters[0] if len(set(iters)) == 1 else iters,
+                "final_rel_rho_u": stats[-1]["rel_rho_u"], "final_rel_rho_m": stats[-1]["rel_rho_m"],
+                "status": stats[-1]["status"], "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"})
+    line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(1e3 * t_total / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": cfg, "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": round(e2e_value, 4), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line))
+    plan.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

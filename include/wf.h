@@ -1,0 +1,281 @@
+/*
+ * wf.h -- C ABI of the GB300 multi-messenger Wiener-filter library (libwf.so).
+ *
+ * Method: Huffenberger 2017, "Preconditioner-free Wiener filtering with a
+ * dense noise matrix" (arXiv:1704.00865).  The Wiener filter
+ *     s = (S^-1 + N^-1)^-1 N^-1 d                           (Sec. 1, eq. wiener)
+ * is found by the messenger iteration of Sec. 2 (eqs. 2mess_t1 - 2mess_s),
+ * generalised to a noise covariance N = N_1f + N_stripe + N_white that is a
+ * sum of parts, each diagonal in its own basis (Sec. 2: "each additional
+ * piece ... two additional fields"; Appendix A, eq. 2mess_prob):
+ *
+ *   part "2DF"  isotropic 1/f noise, diagonal in the 2D DFT of the map;
+ *   part "RF"   horizontal stripes, diagonal in the row-wise 1D DFT along x;
+ *   part "PX"   white noise, diagonal in pixels; infinite at masked pixels
+ *               (Sec. 3.2, Sec. 3.3: a mask is infinite noise variance).
+ *
+ * The signal covariance S is diagonal in the 2D DFT.  Messenger covariances
+ * are T_i = lambda * tau_i * I with tau_i = theta_i * (minimum eigenvalue of
+ * part i) (Sec. 2, Appendix A), Nbar_i = N_i - tau_i held fixed while the
+ * cooling parameter lambda is lowered to 1 (Sec. 2), by a fixed schedule or
+ * by the adaptive rule of Sec. 3.3.
+ *
+ * Maps are real, row-major [ny][nx] float32 (x fastest).  Spectral inputs are
+ * eigenvalues (they do not depend on how the DFT is normalised) in the
+ * half-spectrum layout [ny][nx/2+1] of a real 2D DFT: row ky in FFT order
+ * (0, 1, ..., ny/2, -ny/2+1, ..., -1), column kx = 0..nx/2.  Columns kx = 0
+ * and kx = nx/2 must be symmetric in ky (a real covariance); others need not.
+ *
+ * Memory: every array argument may be a device pointer or a host pointer;
+ * the library asks the CUDA runtime which one it is.  Host arrays are copied
+ * to the plan's device workspace (and s_out back) on the plan's stream.
+ * The caller keeps ownership of every array.  All calls are stream-ordered
+ * on the plan's stream; calls that return results (wf_solve, wf_run,
+ * wf_residual, wf_get_field, wf_fft2) synchronise that stream before they
+ * return.  A plan is not thread-safe: use one plan per host thread.
+ *
+ * Sizes: nx and ny are powers of two in [32, 4096].
+ *
+ * Errors: every function returns WF_OK (0) or one of the codes below;
+ * wf_strerror() gives a message.  On error nothing is written to outputs
+ * except where stated.
+ */
+#ifndef WF_H
+#define WF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define WF_ABI_VERSION 1
+
+#if defined(__GNUC__)
+#define WF_API __attribute__((visibility("default")))
+#else
+#define WF_API
+#endif
+
+enum wf_status {
+  WF_OK = 0,
+  WF_EINVAL = 1,      /* bad size, NULL, NaN/Inf input, asymmetric spectrum   */
+  WF_ENOTPD = 2,      /* a covariance eigenvalue <= 0: C, P1f, Pst, pixel_var  */
+  WF_ENOCONV = 3,     /* max_iters reached; s_out still holds the last iterate */
+  WF_ETIMEOUT = 4,    /* a bounded device wait gave up                          */
+  WF_ECUDA = 5,       /* a CUDA runtime call failed                             */
+  WF_ENOMEM = 6,      /* device allocation failed                               */
+  WF_EUNSUPPORTED = 7 /* size or option this build does not handle             */
+};
+
+/* noise parts present (bit mask); WF_PART_WHITE is required */
+enum { WF_PART_WHITE = 1, WF_PART_1F = 2, WF_PART_STRIPE = 4 };
+
+/* cooling schedules */
+enum { WF_SCHED_FIXED = 0, WF_SCHED_ADAPTIVE = 1 };
+
+/* fields that wf_get_field can return (in pixel space) */
+enum {
+  WF_FIELD_S = 0,      /* the signal estimate s (eq. 2mess_s)                  */
+  WF_FIELD_T_2DF = 1,  /* messenger of the 1/f part (t_0 in eq. 2mess_t0)     */
+  WF_FIELD_D_2DF = 2,  /* data-like field next to it (d_0 in eq. 2mess_d0)    */
+  WF_FIELD_T_RF = 3,   /* messenger of the stripe part                         */
+  WF_FIELD_D_RF = 4    /* data-like field next to it                           */
+};
+
+/*
+ * Cooling schedule (Sec. 2: T_i -> lambda T_i with Nbar_i fixed).
+ * WF_SCHED_FIXED: level j runs iters[j] iterations at lambda = lam[j]
+ *   (host arrays, nlevels <= 256); level changes happen at residual
+ *   checkpoints; after the last level lambda = 1 until convergence.
+ * WF_SCHED_ADAPTIVE (Sec. 3.3): lambda starts at lam0; at each checkpoint,
+ *   if the per-iteration relative change of Delta d^T Delta d is below
+ *   ratio, lambda <- lambda^expo, and lambda = 1 once it falls below snap.
+ *   The paper's values are lam0 = 5e5, ratio = 1e-2, expo = 0.7.
+ */
+typedef struct {
+  int mode;
+  const double* lam;
+  const int* iters;
+  int nlevels;
+  double lam0, ratio, expo, snap;
+} wf_schedule;
+
+/*
+ * Solver parameters (pass NULL to wf_plan_create for the defaults given).
+ *  theta[3]        tau_i = theta_i * min eigenvalue of part i, for the parts
+ *                  (2DF, RF, PX); defaults 0.9, 0.9, 1.0.  theta < 1 is
+ *                  required for interior parts (2DF, RF): at theta = 1 the
+ *                  minimum-eigenvalue mode has Nbar = 0 and never moves.
+ *  split_f         fraction of min(P1f) moved from the 1/f part to the stripe
+ *                  part (a white floor is diagonal in every basis, so N is
+ *                  unchanged); default 0.5.
+ *  split_w         fraction of min(pixel_var) moved from the white part to
+ *                  the stripe part; default 0.
+ *  tol_u_scale     the stop test asks ||Delta d_u||/||d_u|| <= tol * tol_u_scale
+ *                  and ||(S^-1 s)_m|| / ||S^-1 s|| <= tol; default 1.
+ *  merge_2df       1: update s, t_2DF and d_2DF jointly given t_RF (the
+ *                  1/f part and S share the 2D Fourier basis, Appendix A:
+ *                  t_0 is marginalised and s = (S^-1 + N_0^-1)^-1 N_0^-1 d_0);
+ *                  the iteration then needs no tau for the 1/f part and
+ *                  split_f may be 1.  0: the plain sweep.  Default 1.
+ *  residual_every  R: the residual and the lambda rule run every R
+ *                  iterations; default 10.
+ *  max_iters       default 200000.
+ *  check_every     residual checkpoints between host polls of the done flag
+ *                  (latency of the stop test versus host round trips);
+ *                  default 8.
+ */
+typedef struct {
+  double theta[3];
+  double split_f;
+  double split_w;
+  double tol_u_scale;
+  int residual_every;
+  int max_iters;
+  int check_every;
+  int merge_2df;
+  int reserved[4];
+} wf_params;
+
+/* Results of a solve. */
+typedef struct {
+  int iters;            /* iterations run                                     */
+  int checkpoints;      /* residual evaluations                               */
+  double lam_final;     /* lambda at exit (1 when converged)                  */
+  double rel_rho_u;     /* ||Delta d_unmasked|| / ||d_unmasked|| at exit        */
+  double rel_rho_m;     /* ||S^-1 s on masked pixels|| / ||S^-1 s|| at exit    */
+  double tau[3];        /* tau_i used (2DF, RF, PX); 0 for absent parts       */
+  int status;           /* WF_OK or WF_ENOCONV                                */
+  int parts;            /* parts bit mask                                     */
+} wf_stats;
+
+typedef struct wf_plan_s* wf_plan_t;
+
+/* Library ABI version (WF_ABI_VERSION). */
+WF_API int wf_version(void);
+
+/* Message for a status code (static string). */
+WF_API const char* wf_strerror(int status);
+
+/*
+ * wf_params_default -- fill *p with the defaults listed at wf_params.
+ */
+WF_API void wf_params_default(wf_params* p);
+
+/*
+ * wf_plan_create -- make a plan for ny x nx maps with the given noise parts.
+ *   out     receives the plan handle (unchanged on error)
+ *   parts   WF_PART_WHITE | optional WF_PART_1F | optional WF_PART_STRIPE
+ *   p       parameters or NULL for defaults
+ *   stream  cudaStream_t the plan's work runs on (NULL: the legacy default)
+ * Allocates the plan's device workspace (about 12 maps of 4*ny*nx bytes)
+ * with cudaMalloc on the current device.
+ */
+WF_API int wf_plan_create(wf_plan_t* out, int ny, int nx, unsigned parts,
+                   const wf_params* p, void* stream);
+
+/* Release a plan and its workspace (NULL is ignored). */
+WF_API void wf_plan_destroy(wf_plan_t plan);
+
+/*
+ * wf_set_problem -- load one problem into the plan (setup step): copies and
+ * validates the inputs, computes tau_i as theta_i x the minimum eigenvalue
+ * of each part (Sec. 2) and zeroes the messenger fields (Sec. 2: the
+ * iteration starts from s = t0 = d0 = 0).
+ *   d          [ny][nx] data; ignored at masked pixels
+ *   pixel_var  [ny][nx] white-noise variance (> 0 at unmasked pixels)
+ *   mask       [ny][nx] bytes, nonzero = masked; or NULL
+ *   C          [ny][nx/2+1] signal eigenvalues (> 0)
+ *   P1f        [ny][nx/2+1] 1/f eigenvalues (> 0); NULL iff no WF_PART_1F
+ *   Pst        [nx/2+1] stripe eigenvalues per kx (> 0); NULL iff no
+ *              WF_PART_STRIPE
+ *   stripe_amp2 [ny] per-row factor a(y)^2 (> 0) of the stripe part, or NULL
+ *              for 1: the stripe eigenvalue of mode (y, kx) is a(y)^2 Pst[kx]
+ * Returns WF_EINVAL / WF_ENOTPD for invalid inputs (checked on the device).
+ */
+WF_API int wf_set_problem(wf_plan_t plan, const float* d, const float* pixel_var,
+                   const uint8_t* mask, const float* C, const float* P1f,
+                   const float* Pst, const float* stripe_amp2);
+
+/*
+ * wf_run -- run the messenger iteration on the loaded problem until the
+ * schedule ends at lambda = 1 and both ||Delta d_u||/||d_u|| <= tol and
+ * ||(S^-1 s)_masked|| / ||S^-1 s|| <= tol at a checkpoint (Sec. 2: Delta d =
+ * (I + N S^-1) s - d; on masked pixels the residual is S^-1 s), or until
+ * max_iters.  tol <= 0 runs exactly max_iters iterations (no stop test).
+ * Continues from the current state (call wf_set_problem to restart).
+ * Fills *st if not NULL.  Returns WF_OK or WF_ENOCONV.
+ */
+WF_API int wf_run(wf_plan_t plan, const wf_schedule* sched, double tol, wf_stats* st);
+
+/*
+ * wf_iterate -- run exactly n iterations at fixed lambda (no residual, no
+ * stop test): one iteration is the sweep t_PX, d_RF, t_RF, d_2DF, t_2DF, s
+ * of eqs. (2mess_t1)-(2mess_s) generalised to the present parts.
+ */
+WF_API int wf_iterate(wf_plan_t plan, double lam, int n);
+
+/*
+ * wf_residual -- evaluate the residual of the current iterate: rel_rho_u =
+ * ||Delta d_unmasked|| / ||d_unmasked||, rel_rho_m = ||(S^-1 s)_masked|| /
+ * ||S^-1 s|| (Sec. 2, reconstructed data).  Either pointer may be NULL.
+ */
+WF_API int wf_residual(wf_plan_t plan, double* rel_rho_u, double* rel_rho_m);
+
+/*
+ * wf_get_field -- write one field of the current state, in pixel space, to
+ * out [ny][nx] (device or host).  Fields absent from the plan's parts give
+ * WF_EINVAL (and WF_FIELD_T_2DF with merge_2df, where t_2DF is marginalised).
+ */
+WF_API int wf_get_field(wf_plan_t plan, int field, float* out);
+
+/*
+ * wf_solve -- wf_set_problem + wf_run + wf_get_field(WF_FIELD_S): the whole
+ * Wiener filter for one map.  s_out [ny][nx] receives s (also when the
+ * return value is WF_ENOCONV).  st may be NULL.
+ */
+WF_API int wf_solve(wf_plan_t plan, const float* d, const float* pixel_var,
+             const uint8_t* mask, const float* C, const float* P1f,
+             const float* Pst, const float* stripe_amp2,
+             const wf_schedule* sched, double tol, float* s_out,
+             wf_stats* st);
+
+/*
+ * wf_fft2 -- the plan's transforms on their own (the basis changes of Sec. 2,
+ * flat-sky stand-ins for the paper's spherical-harmonic transforms).
+ *   inverse = 0: in = real map [ny][nx], out = spectrum [ny][nx/2] complex
+ *                (interleaved float pairs), unnormalised forward DFT.
+ *   inverse = 1: in = spectrum, out = real map, with the 1/(ny nx) factor.
+ * Spectrum layout: column kx (1 <= kx < nx/2) holds X[ky][kx]; column 0
+ * holds Z[ky] = A[ky] + i B[ky], where A = X[.][0] and B = X[.][nx/2] (the
+ * two real-signal columns packed into one complex column).
+ *   rows_only = 1: only the row-wise transform (the stripe basis): in the
+ *                same layout, column 0 holds (X[y][0], X[y][nx/2]) as a
+ *                real pair per row.
+ */
+WF_API int wf_fft2(wf_plan_t plan, const float* in, float* out, int inverse,
+            int rows_only);
+
+/*
+ * wf_launch_count -- number of CUDA kernels the plan has launched since it
+ * was created (measurement aid: launches inside a timed region are the
+ * difference of two calls).  Returns -1 for a NULL plan.
+ */
+WF_API long long wf_launch_count(wf_plan_t plan);
+
+/*
+ * wf_time_passes -- measurement aid: run n further iterations at fixed
+ * lambda (as wf_iterate) with CUDA events recorded on the plan's stream
+ * around every row pass and every column pass, and return the mean event
+ * time of each pass in microseconds.  Changes the state like wf_iterate.
+ */
+WF_API int wf_time_passes(wf_plan_t plan, double lam, int n, double* us_row,
+                          double* us_col);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WF_H */

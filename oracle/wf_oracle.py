@@ -179,16 +179,21 @@ class Parts:
     N0_full: Optional[np.ndarray]   # original parts (before moves), for N itself
     N1_full: Optional[np.ndarray]
     var: np.ndarray           # [ny][nx] pixel variance (unmasked values)
+    merge_2df: bool = False   # 2DF block updated jointly (Appendix A shortcut)
 
 
 def build_parts(prob, theta: Sequence[float] = DEFAULT_THETA, split_f: float = DEFAULT_SPLIT_F,
-                split_w: float = 0.0) -> Parts:
+                split_w: float = 0.0, merge_2df: bool = False) -> Parts:
     """Messenger covariances of Sec. 2: T_i = tau_i I with tau_i = theta_i x the
     minimum eigenvalue of N_i (Sec. 2, Appendix A), Nbar_i = N_i - tau_i.
 
     ``split_f`` moves split_f * min(P1f) of white floor from the 2DF part to
     the RF part; ``split_w`` moves split_w * min(pixel_var) from the PX part to
     the RF part.  Both leave N = sum_i N_i unchanged.
+
+    ``merge_2df``: the 2DF part needs no messenger covariance of its own (its
+    tau is 0 and Nbar is the whole, possibly reduced, 1/f part): the sweep
+    updates s, t_0 and d_0 together (see Chain.sweep).
     """
     d = np.asarray(prob.d, dtype=np.float64)
     ny, nx = d.shape
@@ -213,7 +218,7 @@ def build_parts(prob, theta: Sequence[float] = DEFAULT_THETA, split_f: float = D
     th_f, th_s, th_p = theta
     if have_f:
         n0 = N0 - w_f
-        tau = th_f * float(n0.min())
+        tau = 0.0 if merge_2df else th_f * float(n0.min())
         parts.append(Part("2DF", n0, tau, n0 - tau))
     if have_s:
         n1 = N1 + w_f + w_w
@@ -223,7 +228,8 @@ def build_parts(prob, theta: Sequence[float] = DEFAULT_THETA, split_f: float = D
     tau = th_p * float(n2[unmasked].min())
     parts.append(Part("PX", n2, tau, np.where(unmasked, n2 - tau, np.inf)))
     dd = np.where(unmasked, d, 0.0)
-    return Parts(ny, nx, C, parts, unmasked, dd, N0, N1, np.where(unmasked, var, 0.0))
+    return Parts(ny, nx, C, parts, unmasked, dd, N0, N1, np.where(unmasked, var, 0.0),
+                 merge_2df=bool(merge_2df and have_f))
 
 
 def to_basis(name: str, x: np.ndarray) -> np.ndarray:
@@ -293,7 +299,17 @@ class Chain:
         """One iteration: eqs. (2mess_t1), (2mess_d0), (2mess_t0), (2mess_s),
         generalised, from the data end to the signal: t_{K-1}, d_{K-2}, ...,
         t_0, s.  Each update is computed in the basis where its covariances
-        are diagonal (Sec. 2)."""
+        are diagonal (Sec. 2).
+
+        With ``merge_2df`` the last three updates are replaced by the joint
+        conditional mean of (s, t_0, d_0) given t_1 -- possible because S and
+        the 2DF part share a basis (Appendix A: the t_0 updates can be combined
+        there, and s = (S^-1 + N_0^-1)^-1 N_0^-1 d_0).  Marginalising t_0
+        leaves s -N_0- d_0 -T_1- t_1, so
+            d_0 = (C + N_0) / (C + N_0 + T_1) t_1,   s = C / (C + N_0) d_0.
+        """
+        if self.P.merge_2df:
+            return self._sweep_merged(lam, on_update)
         P = self.P
         for i in range(self.K - 1, -1, -1):
             part = P.parts[i]
@@ -321,11 +337,46 @@ class Chain:
         if on_update is not None:
             on_update("s")
 
+    def _sweep_merged(self, lam: float, on_update=None) -> None:
+        P = self.P
+        for i in range(self.K - 1, 0, -1):
+            part = P.parts[i]
+            b = part.name
+            t = _link_mean(part.Nbar, to_basis(b, self.dd[i]), self.T(i, lam), to_basis(b, self.dd[i - 1]))
+            self.t[i] = from_basis(b, t)
+            if on_update is not None:
+                on_update(f"t{i}")
+            if i > 1:
+                prev = P.parts[i - 1]
+                pb = prev.name
+                dprev = _link_mean(self.T(i, lam), to_basis(pb, self.t[i]), prev.Nbar,
+                                   to_basis(pb, self.t[i - 1]))
+                self.dd[i - 1] = from_basis(pb, dprev)
+                if on_update is not None:
+                    on_update(f"d{i - 1}")
+        N0 = P.parts[0].N
+        T1 = self.T(1, lam)
+        D0 = (P.C + N0) / (P.C + N0 + T1) * to_basis("2DF", self.t[1])
+        self.dd[0] = from_basis("2DF", D0)
+        self.s = from_basis("2DF", P.C / (P.C + N0) * D0)
+        # t_0 is marginalised; keep the field defined as s (its T_0 = 0 limit)
+        self.t[0] = self.s
+        self.iters += 1
+        if on_update is not None:
+            on_update("s")
+
     # --- augmented objective (Appendix A, eq. 2mess_prob) ------------------
     def chi2_aug(self, lam: float) -> float:
         P = self.P
         tot = _quad("2DF", self.s, 1.0 / P.C)
+        if P.merge_2df:
+            # t_0 marginalised: s -N_0- d_0 replaces s -T_0- t_0 -Nbar_0- d_0
+            with np.errstate(divide="ignore"):
+                w0 = np.where(P.parts[0].N > 0, 1.0 / P.parts[0].N, 0.0)
+            tot += _quad("2DF", self.dd[0] - self.s, w0)
         for i, part in enumerate(P.parts):
+            if P.merge_2df and i == 0:
+                continue
             sig_side = self.dd[i - 1] if i > 0 else self.s
             tot += _quad("PX", self.t[i] - sig_side, np.full((P.ny, P.nx), 1.0 / self.T(i, lam)))
             # Nbar = inf (masked) contributes nothing; Nbar = 0 pins d = t
@@ -412,7 +463,7 @@ def fixed_schedule(lams: Sequence[float], iters: Sequence[int]):
 def messenger_solve(prob, *, theta=DEFAULT_THETA, split_f=DEFAULT_SPLIT_F, split_w=0.0,
                     schedule=None, tol=1e-6, residual_every=10, max_iters=20000,
                     n_iters: Optional[int] = None, P: Optional[Parts] = None,
-                    trace: bool = False):
+                    trace: bool = False, merge_2df: bool = False):
     """Run the messenger iteration (Sec. 2) with a cooling schedule.
 
     schedule: dict(mode="fixed", lam=[...], iters=[...]) -- each level j runs
@@ -424,7 +475,7 @@ def messenger_solve(prob, *, theta=DEFAULT_THETA, split_f=DEFAULT_SPLIT_F, split
     ``n_iters`` runs exactly that many iterations and ignores tol.
     """
     if P is None:
-        P = build_parts(prob, theta, split_f, split_w)
+        P = build_parts(prob, theta, split_f, split_w, merge_2df)
     ch = Chain(P)
     if schedule is None:
         schedule = dict(mode="adaptive", **ADAPTIVE_DEFAULT)

@@ -1,0 +1,639 @@
+// wf_api.cu -- host side of the C ABI declared in include/wf.h: plans,
+// workspace, input staging, the iteration driver and the exports.
+//
+// One iteration (Huffenberger 2017, Sec. 2, eqs. 2mess_t1 - 2mess_s for the
+// chain s -T0- t_2DF -Nb0- d_2DF -T1- t_RF -Nb1- d_RF -T2- t_PX -Nb2- d) is
+// two launches: the row pass (t_PX between the inverse and forward row
+// transforms, then d_RF, t_RF) and the column pass (d_2DF, t_2DF between the
+// forward and inverse column transforms; s implicit).  Every R iterations
+// the residual (Sec. 2, Delta d) and the lambda controller run on the device.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "../../include/wf.h"
+#include "wf_device.cuh"
+#include "wf_internal.h"
+
+using namespace wf;
+
+struct wf_plan_s {
+  int ny = 0, nx = 0, M = 0;
+  unsigned parts = 0;
+  bool has_f = false, has_rf = false, merge = false, loaded = false;
+  wf_params p{};
+  cudaStream_t stream = nullptr;
+  int nrow = 0;
+  long long it_done = 0;
+  long long launches = 0;   // kernels launched by this plan
+  // device workspace
+  float4* dn = nullptr;
+  float2 *f_d1 = nullptr, *f_t1 = nullptr, *f_x = nullptr, *f_y = nullptr, *f_t0 = nullptr;
+  float2 *eig = nullptr, *eig_nyq = nullptr;
+  float *pst = nullptr, *a2 = nullptr;
+  float2 *twx = nullptr, *twy = nullptr;
+  float2 *r_g = nullptr, *r_q = nullptr;
+  double* part = nullptr;
+  WfState* st = nullptr;
+  double* lam_sched = nullptr;
+  int* it_sched = nullptr;
+  // staging for host-resident arguments
+  float *stg_d = nullptr, *stg_var = nullptr, *stg_C = nullptr, *stg_P = nullptr;
+  float *stg_pst = nullptr, *stg_a2 = nullptr, *stg_io = nullptr;
+  uint8_t* stg_mask = nullptr;
+  WfState* h_st = nullptr;  // pinned
+  std::vector<void*> allocs;
+};
+
+#define CK(x)                                      \
+  do {                                             \
+    cudaError_t e_ = (x);                          \
+    if (e_ != cudaSuccess) {                       \
+      fprintf(stderr, "libwf: %s:%d %s: %s\n", __FILE__, __LINE__, #x, cudaGetErrorString(e_)); \
+      return e_ == cudaErrorMemoryAllocation ? WF_ENOMEM : WF_ECUDA; \
+    }                                              \
+  } while (0)
+#define CKI(x)                                     \
+  do {                                             \
+    int e_ = (x);                                  \
+    if (e_ != 0) {                                 \
+      fprintf(stderr, "libwf: %s:%d launch: %s\n", __FILE__, __LINE__, cudaGetErrorString((cudaError_t)e_)); \
+      return WF_ECUDA;                             \
+    }                                              \
+  } while (0)
+
+template <class T>
+static int dalloc(wf_plan_s* P, T** out, size_t n) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, n * sizeof(T) + 16);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return WF_ENOMEM;
+  }
+  P->allocs.push_back(q);
+  *out = (T*)q;
+  return WF_OK;
+}
+
+static bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// device view of a caller array: the array itself, or a staged copy
+template <class T>
+static int to_device(wf_plan_s* P, const T* src, T* stage, size_t n, const T** out) {
+  if (src == nullptr) {
+    *out = nullptr;
+    return WF_OK;
+  }
+  if (is_device_ptr(src)) {
+    *out = src;
+    return WF_OK;
+  }
+  CK(cudaMemcpyAsync(stage, src, n * sizeof(T), cudaMemcpyHostToDevice, P->stream));
+  *out = stage;
+  return WF_OK;
+}
+
+extern "C" {
+
+int wf_version(void) { return WF_ABI_VERSION; }
+
+const char* wf_strerror(int s) {
+  switch (s) {
+    case WF_OK: return "ok";
+    case WF_EINVAL: return "invalid argument (size, NULL, non-finite or asymmetric input)";
+    case WF_ENOTPD: return "a covariance eigenvalue is not positive";
+    case WF_ENOCONV: return "no convergence within max_iters";
+    case WF_ETIMEOUT: return "a device wait timed out";
+    case WF_ECUDA: return "CUDA runtime error";
+    case WF_ENOMEM: return "device allocation failed";
+    case WF_EUNSUPPORTED: return "unsupported size or option";
+    default: return "unknown status";
+  }
+}
+
+void wf_params_default(wf_params* p) {
+  if (!p) return;
+  memset(p, 0, sizeof(*p));
+  p->theta[0] = 0.9;
+  p->theta[1] = 0.9;
+  p->theta[2] = 1.0;
+  p->split_f = 0.5;
+  p->split_w = 0.0;
+  p->tol_u_scale = 1.0;
+  p->merge_2df = 1;
+  p->residual_every = 10;
+  p->max_iters = 200000;
+  p->check_every = 8;
+}
+
+void wf_plan_destroy(wf_plan_t P) {
+  if (!P) return;
+  for (void* q : P->allocs) cudaFree(q);
+  if (P->h_st) cudaFreeHost(P->h_st);
+  delete P;
+}
+
+int wf_plan_create(wf_plan_t* out, int ny, int nx, unsigned parts, const wf_params* p, void* stream) {
+  if (!out) return WF_EINVAL;
+  if (!size_supported(nx) || !size_supported(ny)) return WF_EUNSUPPORTED;
+  if (!(parts & WF_PART_WHITE) || (parts & ~7u)) return WF_EINVAL;
+  wf_params prm;
+  if (p) prm = *p;
+  else wf_params_default(&prm);
+  if (prm.residual_every < 1 || prm.max_iters < 1 || prm.check_every < 1) return WF_EINVAL;
+  for (int i = 0; i < 3; ++i)
+    if (!(prm.theta[i] > 0.0 && prm.theta[i] <= 1.0)) return WF_EINVAL;
+  // the plain sweep needs tau_2DF > 0, i.e. split_f < 1; merged, N0 may reach 0
+  const double fmax = prm.merge_2df ? 1.0 : 0.999999;
+  if (!(prm.split_f >= 0.0 && prm.split_f <= fmax) || !(prm.split_w >= 0.0 && prm.split_w < 1.0)) return WF_EINVAL;
+  if (!(prm.tol_u_scale > 0.0) || (prm.merge_2df != 0 && prm.merge_2df != 1)) return WF_EINVAL;
+
+  wf_plan_s* P = new wf_plan_s();
+  P->ny = ny;
+  P->nx = nx;
+  P->M = nx / 2;
+  P->parts = parts;
+  P->has_f = parts & WF_PART_1F;
+  P->has_rf = parts & WF_PART_STRIPE;
+  P->merge = P->has_f && prm.merge_2df;
+  P->p = prm;
+  P->stream = (cudaStream_t)stream;
+  P->nrow = row_grid(nx, ny);
+  const size_t npx = (size_t)ny * nx, nh = (size_t)ny * P->M;
+  int rc = WF_OK;
+#define AL(ptr, n)                                   \
+  if (rc == WF_OK) rc = dalloc(P, &(ptr), (n));
+  AL(P->dn, npx / 2);
+  AL(P->f_x, nh);
+  if (P->has_rf) {
+    AL(P->f_d1, nh);
+    AL(P->f_t1, nh);
+  } else {
+    AL(P->f_y, nh);
+  }
+  if (P->has_f && !P->merge) AL(P->f_t0, nh);
+  AL(P->eig, nh);
+  AL(P->eig_nyq, (size_t)ny);
+  AL(P->pst, (size_t)P->M + 1);
+  AL(P->a2, (size_t)ny);
+  AL(P->twx, (size_t)nx);
+  AL(P->twy, (size_t)ny);
+  AL(P->r_g, nh);
+  AL(P->r_q, nh);
+  AL(P->part, (size_t)3 * P->nrow + 4 * 256 + 64);
+  AL(P->st, (size_t)1);
+  AL(P->lam_sched, (size_t)260);
+  AL(P->it_sched, (size_t)260);
+  AL(P->stg_d, npx);
+  AL(P->stg_var, npx);
+  AL(P->stg_mask, npx);
+  AL(P->stg_C, (size_t)ny * (P->M + 1));
+  if (P->has_f) AL(P->stg_P, (size_t)ny * (P->M + 1));
+  AL(P->stg_pst, (size_t)P->M + 1);
+  AL(P->stg_a2, (size_t)ny);
+  AL(P->stg_io, npx + 64);
+#undef AL
+  if (rc != WF_OK) {
+    wf_plan_destroy(P);
+    return rc;
+  }
+  if (cudaMallocHost(&P->h_st, sizeof(WfState)) != cudaSuccess) {
+    cudaGetLastError();
+    P->h_st = nullptr;
+    wf_plan_destroy(P);
+    return WF_ENOMEM;
+  }
+  // twiddle tables exp(-2 pi i k / n), computed in double on the host
+  std::vector<float2> tx(nx), ty(ny);
+  for (int k = 0; k < nx; ++k) {
+    const double a = 2.0 * M_PI * (double)k / (double)nx;
+    tx[k] = make_float2((float)cos(a), (float)-sin(a));
+  }
+  for (int k = 0; k < ny; ++k) {
+    const double a = 2.0 * M_PI * (double)k / (double)ny;
+    ty[k] = make_float2((float)cos(a), (float)-sin(a));
+  }
+  cudaError_t e1 = cudaMemcpy(P->twx, tx.data(), nx * sizeof(float2), cudaMemcpyHostToDevice);
+  cudaError_t e2 = cudaMemcpy(P->twy, ty.data(), ny * sizeof(float2), cudaMemcpyHostToDevice);
+  if (e1 != cudaSuccess || e2 != cudaSuccess) {
+    wf_plan_destroy(P);
+    return WF_ECUDA;
+  }
+  *out = P;
+  return WF_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- helpers
+static RowArgs row_args(wf_plan_s* P) {
+  RowArgs a{};
+  a.ny = P->ny;
+  a.nx = P->nx;
+  a.has_rf = P->has_rf;
+  a.dn = P->dn;
+  a.f_d1 = P->f_d1;
+  a.f_t1 = P->f_t1;
+  a.f_x = P->f_x;
+  a.f_y = P->f_y;
+  a.pst = P->pst;
+  a.a2 = P->a2;
+  a.twx = P->twx;
+  a.st = P->st;
+  a.r_g = P->r_g;
+  a.r_q = P->r_q;
+  return a;
+}
+
+static ColArgs col_args(wf_plan_s* P, int parity) {
+  ColArgs a{};
+  a.ny = P->ny;
+  a.nx = P->nx;
+  a.has_rf = P->has_rf;
+  a.has_f = P->has_f;
+  a.merge = P->merge;
+  a.parity = parity & 1;
+  a.f_y = P->has_rf ? P->f_t1 : P->f_y;
+  a.f_x = P->f_x;
+  a.f_t0 = P->f_t0;
+  a.eig = P->eig;
+  a.eig_nyq = P->eig_nyq;
+  a.twy = P->twy;
+  a.st = P->st;
+  a.r_g = P->r_g;
+  a.r_q = P->r_q;
+  return a;
+}
+
+// one sweep: row pass then column pass
+static int enqueue_row_pass(wf_plan_s* P) {
+  RowArgs ra = row_args(P);
+  ra.check_done = 1;
+  CKI(launch_row(P->has_rf ? ROW_PASS_RF : ROW_PASS_NORF, ra, P->stream));
+  P->launches += 1;
+  return WF_OK;
+}
+
+static int enqueue_col_pass(wf_plan_s* P, int parity) {
+  ColArgs ca = col_args(P, parity);
+  ca.check_done = 1;
+  CKI(launch_col(P->merge ? COL_PASS_MERGE : (P->has_f ? COL_PASS_2DF : COL_PASS_NO2DF), ca, P->stream));
+  P->launches += 1;
+  return WF_OK;
+}
+
+static int enqueue_iteration(wf_plan_s* P, int parity) {
+  int rc = enqueue_row_pass(P);
+  if (rc) return rc;
+  return enqueue_col_pass(P, parity);
+}
+
+// residual passes; partials land in part[0 .. 3 nrow)
+static int enqueue_residual(wf_plan_s* P, int parity, int check_done) {
+  ColArgs ca = col_args(P, parity);
+  ca.check_done = check_done;
+  CKI(launch_col(COL_RESID_A, ca, P->stream));
+  RowArgs ra = row_args(P);
+  ra.check_done = check_done;
+  ra.part0 = P->part;
+  ra.part1 = P->part + P->nrow;
+  CKI(launch_row(ROW_RESID_B, ra, P->stream));
+  if (P->has_f) CKI(launch_col(COL_RESID_C, ca, P->stream));
+  ra.part0 = P->part + 2 * P->nrow;
+  CKI(launch_row(ROW_RESID_D, ra, P->stream));
+  P->launches += P->has_f ? 4 : 3;
+  return WF_OK;
+}
+
+static CtrlArgs ctrl_args(wf_plan_s* P) {
+  CtrlArgs c{};
+  c.st = P->st;
+  c.part_g = P->part;
+  c.part_g2 = P->part + P->nrow;
+  c.part_rho = P->part + 2 * P->nrow;
+  c.nrow = P->nrow;
+  c.R = P->p.residual_every;
+  c.max_iters = P->p.max_iters;
+  c.lam_sched = P->lam_sched;
+  c.it_sched = P->it_sched;
+  return c;
+}
+
+static int finish_status(unsigned err) {
+  if (err & (WF_ERR_VAR | WF_ERR_C | WF_ERR_P1F | WF_ERR_PST | WF_ERR_A2)) return WF_ENOTPD;
+  if (err) return WF_EINVAL;
+  return WF_OK;
+}
+
+extern "C" {
+
+int wf_set_problem(wf_plan_t P, const float* d, const float* pixel_var, const uint8_t* mask,
+                   const float* C, const float* P1f, const float* Pst, const float* stripe_amp2) {
+  if (!P || !d || !pixel_var || !C) return WF_EINVAL;
+  if (P->has_f != (P1f != nullptr)) return WF_EINVAL;
+  if (P->has_rf != (Pst != nullptr)) return WF_EINVAL;
+  if (!P->has_rf && stripe_amp2) return WF_EINVAL;
+  const size_t npx = (size_t)P->ny * P->nx, nspec = (size_t)P->ny * (P->M + 1);
+  SetupArgs a{};
+  a.ny = P->ny;
+  a.nx = P->nx;
+  int rc;
+  if ((rc = to_device(P, d, P->stg_d, npx, &a.d))) return rc;
+  if ((rc = to_device(P, pixel_var, P->stg_var, npx, &a.var))) return rc;
+  if ((rc = to_device(P, mask, P->stg_mask, npx, &a.mask))) return rc;
+  if ((rc = to_device(P, C, P->stg_C, nspec, &a.C))) return rc;
+  if ((rc = to_device(P, P1f, P->stg_P, nspec, &a.P1f))) return rc;
+  if ((rc = to_device(P, Pst, P->stg_pst, (size_t)P->M + 1, &a.Pst))) return rc;
+  if ((rc = to_device(P, stripe_amp2, P->stg_a2, (size_t)P->ny, &a.a2))) return rc;
+  a.dn = P->dn;
+  a.eig = P->eig;
+  a.eig_nyq = P->eig_nyq;
+  a.pst = P->pst;
+  a.a2_out = P->a2;
+  a.part = P->part + 3 * P->nrow;
+  a.st = P->st;
+  for (int i = 0; i < 3; ++i) a.theta[i] = P->p.theta[i];
+  a.split_f = P->p.split_f;
+  a.split_w = P->p.split_w;
+  a.has_rf = P->has_rf;
+  a.has_f = P->has_f;
+  a.merge = P->merge;
+  CK(cudaMemsetAsync(P->st, 0, sizeof(WfState), P->stream));
+  CKI(launch_setup(a, P->stream));
+  P->launches += 5;
+  // iteration starts from zero fields (Sec. 2)
+  const size_t nhb = (size_t)P->ny * P->M * sizeof(float2);
+  CK(cudaMemsetAsync(P->f_x, 0, nhb, P->stream));
+  if (P->f_d1) CK(cudaMemsetAsync(P->f_d1, 0, nhb, P->stream));
+  if (P->f_t1) CK(cudaMemsetAsync(P->f_t1, 0, nhb, P->stream));
+  if (P->f_y) CK(cudaMemsetAsync(P->f_y, 0, nhb, P->stream));
+  if (P->f_t0) CK(cudaMemsetAsync(P->f_t0, 0, nhb, P->stream));
+  CK(cudaMemcpyAsync(P->h_st, P->st, sizeof(WfState), cudaMemcpyDeviceToHost, P->stream));
+  CK(cudaStreamSynchronize(P->stream));
+  P->it_done = 0;
+  P->loaded = false;
+  const int st = finish_status(P->h_st->err);
+  if (st != WF_OK) return st;
+  P->loaded = true;
+  return WF_OK;
+}
+
+int wf_iterate(wf_plan_t P, double lam, int n) {
+  if (!P || !P->loaded || n < 0 || !(lam >= 1.0) || !isfinite(lam)) return WF_EINVAL;
+  CKI(launch_set_lambda(P->st, lam, 1, P->stream));
+  P->launches += 1;
+  for (int i = 0; i < n; ++i) {
+    int rc = enqueue_iteration(P, (int)(P->it_done & 1));
+    if (rc) return rc;
+    P->it_done++;
+  }
+  CK(cudaGetLastError());
+  return WF_OK;
+}
+
+static void fill_stats(wf_plan_s* P, wf_stats* st, int status) {
+  if (!st) return;
+  const WfState& h = *P->h_st;
+  st->iters = h.iter;
+  st->checkpoints = h.checkpoints;
+  st->lam_final = h.lam;
+  st->rel_rho_u = h.rel_u;
+  st->rel_rho_m = h.rel_m;
+  for (int i = 0; i < 3; ++i) st->tau[i] = h.tau[i];
+  st->status = status;
+  st->parts = (int)P->parts;
+}
+
+int wf_run(wf_plan_t P, const wf_schedule* sch, double tol, wf_stats* st) {
+  if (!P || !P->loaded || !sch) return WF_EINVAL;
+  const int R = P->p.residual_every;
+  CtrlArgs c = ctrl_args(P);
+  c.tol = tol;
+  c.tol_u = tol * P->p.tol_u_scale;
+  c.count_iters = 1;
+  c.max_iters = ((P->p.max_iters + R - 1) / R) * R;
+  double lam0;
+  if (sch->mode == WF_SCHED_FIXED) {
+    if (sch->nlevels < 1 || sch->nlevels > 256 || !sch->lam || !sch->iters) return WF_EINVAL;
+    std::vector<double> L(sch->lam, sch->lam + sch->nlevels);
+    std::vector<int> I(sch->iters, sch->iters + sch->nlevels);
+    for (size_t i = 0; i < L.size(); ++i)
+      if (!(L[i] >= 1.0) || !isfinite(L[i]) || I[i] < 0) return WF_EINVAL;
+    if (L.back() != 1.0) {
+      L.push_back(1.0);
+      I.push_back(0);
+    }
+    CK(cudaMemcpyAsync(P->lam_sched, L.data(), L.size() * sizeof(double), cudaMemcpyHostToDevice, P->stream));
+    CK(cudaMemcpyAsync(P->it_sched, I.data(), I.size() * sizeof(int), cudaMemcpyHostToDevice, P->stream));
+    c.mode = 0;
+    c.nlevels = (int)L.size();
+    lam0 = L[0];
+  } else if (sch->mode == WF_SCHED_ADAPTIVE) {
+    if (!(sch->lam0 >= 1.0) || !(sch->expo > 0.0 && sch->expo < 1.0) || !(sch->ratio > 0.0) ||
+        !(sch->snap >= 1.0))
+      return WF_EINVAL;
+    c.mode = 1;
+    c.ratio = sch->ratio;
+    c.expo = sch->expo;
+    c.snap = sch->snap;
+    lam0 = sch->lam0;
+  } else {
+    return WF_EINVAL;
+  }
+  CKI(launch_set_lambda(P->st, lam0, 1, P->stream));
+  P->launches += 1;
+  const long long it0 = P->it_done;
+  long long enq = it0;
+  const int K = P->p.check_every;
+  const long long cap = it0 + (long long)c.max_iters;
+  for (;;) {
+    for (int cp = 0; cp < K && enq < cap; ++cp) {
+      for (int i = 0; i < R; ++i) {
+        int rc = enqueue_iteration(P, (int)(enq & 1));
+        if (rc) return rc;
+        ++enq;
+      }
+      int rc = enqueue_residual(P, (int)(enq & 1), 1);
+      if (rc) return rc;
+      CKI(launch_ctrl(c, P->stream));
+      P->launches += 1;
+    }
+    CK(cudaMemcpyAsync(P->h_st, P->st, sizeof(WfState), cudaMemcpyDeviceToHost, P->stream));
+    CK(cudaStreamSynchronize(P->stream));
+    if (P->h_st->done || enq >= cap) break;
+  }
+  P->it_done = it0 + P->h_st->iter;
+  int status = P->h_st->status == 3 ? WF_ENOCONV : WF_OK;
+  fill_stats(P, st, status);
+  return status;
+}
+
+int wf_residual(wf_plan_t P, double* rel_u, double* rel_m) {
+  if (!P || !P->loaded) return WF_EINVAL;
+  // a residual of the current state, without touching lambda or counters
+  int rc = enqueue_residual(P, (int)(P->it_done & 1), 0);
+  if (rc) return rc;
+  CtrlArgs c = ctrl_args(P);
+  c.count_iters = 0;
+  CKI(launch_ctrl(c, P->stream));
+  P->launches += 1;
+  CK(cudaMemcpyAsync(P->h_st, P->st, sizeof(WfState), cudaMemcpyDeviceToHost, P->stream));
+  CK(cudaStreamSynchronize(P->stream));
+  if (rel_u) *rel_u = P->h_st->rel_u;
+  if (rel_m) *rel_m = P->h_st->rel_m;
+  return WF_OK;
+}
+
+int wf_get_field(wf_plan_t P, int field, float* out) {
+  if (!P || !P->loaded || !out) return WF_EINVAL;
+  const bool dev = is_device_ptr(out);
+  float2* dst = dev ? (float2*)out : (float2*)P->stg_io;
+  RowArgs ra = row_args(P);
+  ra.out_px = dst;
+  switch (field) {
+    case WF_FIELD_S: {
+      if (P->has_f) {
+        ColArgs ca = col_args(P, (int)(P->it_done & 1));
+        CKI(launch_col(COL_RESID_A, ca, P->stream));
+        P->launches += 1;
+        ra.in_rf = P->r_q;
+      } else {
+        ra.in_rf = P->f_x;
+      }
+      break;
+    }
+    case WF_FIELD_T_2DF: {
+      if (!P->has_f || P->merge) return WF_EINVAL;
+      ColArgs ca = col_args(P, 0);
+      ca.in = P->f_t0;
+      ca.out = P->r_g;
+      CKI(launch_col(COL_INV, ca, P->stream));
+      P->launches += 1;
+      ra.in_rf = P->r_g;
+      break;
+    }
+    case WF_FIELD_D_2DF:
+      if (!P->has_f) return WF_EINVAL;
+      ra.in_rf = P->f_x;
+      break;
+    case WF_FIELD_T_RF:
+      if (!P->has_rf) return WF_EINVAL;
+      ra.in_rf = P->f_t1;
+      break;
+    case WF_FIELD_D_RF:
+      if (!P->has_rf) return WF_EINVAL;
+      ra.in_rf = P->f_d1;
+      break;
+    default:
+      return WF_EINVAL;
+  }
+  CKI(launch_row(ROW_C2R, ra, P->stream));
+  P->launches += 1;
+  if (!dev)
+    CK(cudaMemcpyAsync(out, dst, (size_t)P->ny * P->nx * sizeof(float), cudaMemcpyDeviceToHost, P->stream));
+  CK(cudaStreamSynchronize(P->stream));
+  return WF_OK;
+}
+
+int wf_solve(wf_plan_t P, const float* d, const float* pixel_var, const uint8_t* mask, const float* C,
+             const float* P1f, const float* Pst, const float* stripe_amp2, const wf_schedule* sched,
+             double tol, float* s_out, wf_stats* st) {
+  if (!s_out) return WF_EINVAL;
+  int rc = wf_set_problem(P, d, pixel_var, mask, C, P1f, Pst, stripe_amp2);
+  if (rc) return rc;
+  int status = wf_run(P, sched, tol, st);
+  if (status != WF_OK && status != WF_ENOCONV) return status;
+  rc = wf_get_field(P, WF_FIELD_S, s_out);
+  if (rc) return rc;
+  return status;
+}
+
+int wf_fft2(wf_plan_t P, const float* in, float* out, int inverse, int rows_only) {
+  if (!P || !in || !out) return WF_EINVAL;
+  const size_t n = (size_t)P->ny * P->nx;
+  const float* din;
+  int rc = to_device(P, in, P->stg_d, n, &din);
+  if (rc) return rc;
+  const bool dev = is_device_ptr(out);
+  float* dout = dev ? out : P->stg_io;
+  RowArgs ra = row_args(P);
+  ColArgs ca = col_args(P, 0);
+  if (!inverse) {
+    ra.in_px = (const float2*)din;
+    ra.out_rf = rows_only ? (float2*)dout : P->r_g;
+    CKI(launch_row(ROW_R2C, ra, P->stream));
+    P->launches += 1;
+    if (!rows_only) {
+      ca.in = P->r_g;
+      ca.out = (float2*)dout;
+      CKI(launch_col(COL_FWD, ca, P->stream));
+      P->launches += 1;
+    }
+  } else {
+    const float2* rin = (const float2*)din;
+    if (!rows_only) {
+      ca.in = rin;
+      ca.out = P->r_g;
+      CKI(launch_col(COL_INV, ca, P->stream));
+      P->launches += 1;
+      rin = P->r_g;
+    }
+    ra.in_rf = rin;
+    ra.out_px = (float2*)dout;
+    CKI(launch_row(ROW_C2R, ra, P->stream));
+    P->launches += 1;
+  }
+  if (!dev) CK(cudaMemcpyAsync(out, dout, n * sizeof(float), cudaMemcpyDeviceToHost, P->stream));
+  CK(cudaStreamSynchronize(P->stream));
+  return WF_OK;
+}
+
+long long wf_launch_count(wf_plan_t P) { return P ? P->launches : -1; }
+
+int wf_time_passes(wf_plan_t P, double lam, int n, double* us_row, double* us_col) {
+  if (!P || !P->loaded || n < 1 || !(lam >= 1.0) || !isfinite(lam)) return WF_EINVAL;
+  CKI(launch_set_lambda(P->st, lam, 1, P->stream));
+  P->launches += 1;
+  std::vector<cudaEvent_t> ev(3 * (size_t)n);
+  for (auto& e : ev) CK(cudaEventCreate(&e));
+  int rc = WF_OK;
+  for (int i = 0; i < n && rc == WF_OK; ++i) {
+    CK(cudaEventRecord(ev[3 * i], P->stream));
+    rc = enqueue_row_pass(P);
+    if (rc) break;
+    CK(cudaEventRecord(ev[3 * i + 1], P->stream));
+    rc = enqueue_col_pass(P, (int)(P->it_done & 1));
+    if (rc) break;
+    CK(cudaEventRecord(ev[3 * i + 2], P->stream));
+    P->it_done++;
+  }
+  CK(cudaStreamSynchronize(P->stream));
+  double sr = 0.0, sc = 0.0;
+  for (int i = 0; i < n && rc == WF_OK; ++i) {
+    float a = 0.f, b = 0.f;
+    CK(cudaEventElapsedTime(&a, ev[3 * i], ev[3 * i + 1]));
+    CK(cudaEventElapsedTime(&b, ev[3 * i + 1], ev[3 * i + 2]));
+    sr += a;
+    sc += b;
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (rc) return rc;
+  if (us_row) *us_row = 1000.0 * sr / n;
+  if (us_col) *us_col = 1000.0 * sc / n;
+  return WF_OK;
+}
+
+}  // extern "C"

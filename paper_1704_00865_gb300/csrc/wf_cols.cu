@@ -1,0 +1,360 @@
+// wf_cols.cu -- the column pass of the messenger iteration and the column
+// steps of the residual (Huffenberger 2017, Sec. 2).
+//
+// One CTA owns W adjacent complex columns (kx) of a row-transformed field;
+// TPC = ny/E threads per column run a complex length-ny Stockham FFT in shared
+// memory, which completes the 2D DFT.  The 2D-Fourier updates -- eqs.
+// (2mess_d0), (2mess_t0) and (2mess_s) analogues: the 1/f part and the signal
+// prior, both diagonal there -- run between the forward and the inverse
+// column transform.  s is never stored: it is C t0 / (C + T_0) (eq. 2mess_s),
+// recomputed with the T_0 in force when t0 was made.
+//
+// Column 0 packs the two real-signal columns kx = 0 and kx = nx/2 as
+// Z = A + i B; after the column DFT, A[ky] = (Z[ky] + conj Z[-ky])/2 and
+// B[ky] = (Z[ky] - conj Z[-ky])/(2i), which the updates treat as separate
+// modes with their own eigenvalues.
+#include "wf_device.cuh"
+#include "wf_internal.h"
+
+namespace wf {
+
+template <int L>
+struct ColCfg {
+  static constexpr int E = (L >= 2048) ? 16 : 8;
+  static constexpr int TPC = L / E;
+  static constexpr int W0 = 256 / TPC;
+  static constexpr int W = W0 < 1 ? 1 : (W0 > 32 ? 32 : W0);
+  static constexpr int THREADS = W * TPC;
+};
+
+__device__ __forceinline__ void unpack_pair(float2 Z, float2 Zp, float2& A, float2& B) {
+  const float2 cz = cconj(Zp);
+  A = cscale(cadd(Z, cz), 0.5f);
+  const float2 D = cscale(csub(Z, cz), 0.5f);
+  B = make_float2(D.y, -D.x);
+}
+__device__ __forceinline__ float2 repack_pair(float2 A, float2 B) {
+  return make_float2(A.x - B.y, A.y + B.x);
+}
+
+// 2D-Fourier updates of one mode (real coefficients, complex values).
+//   y    : data-side messenger (t_RF, or t_PX without stripes), this basis
+//   t0o  : stored t_2DF;  C, P: signal and 1/f eigenvalues
+// returns d_2DF and writes the new t_2DF
+__device__ __forceinline__ float2 mode_2df(float2 yv, float2 t0o, float C, float P, float off0,
+                                           float Tl, float T0, float T0s, float2& t0n) {
+  const float nb0 = P + off0;                           // Nbar_2DF
+  const float ws = __fdividef(C, C + T0s);              // s = C t0 / (C + T0)
+  const float2 so = cscale(t0o, ws);
+  const float wd = __fdividef(nb0, nb0 + Tl);          // d0 = (Nb y + Tl t0)/(Nb + Tl)
+  const float2 d0 = make_float2(fmaf(wd, yv.x - t0o.x, t0o.x), fmaf(wd, yv.y - t0o.y, t0o.y));
+  const float wt = __fdividef(nb0, nb0 + T0);          // t0 = (T0 d0 + Nb s)/(Nb + T0)
+  t0n = make_float2(fmaf(wt, so.x - d0.x, d0.x), fmaf(wt, so.y - d0.y, d0.y));
+  return d0;
+}
+
+template <int L, int MODE>
+__global__ void __launch_bounds__(ColCfg<L>::THREADS)
+col_kernel(ColArgs a) {
+  using Cfg = ColCfg<L>;
+  constexpr int E = Cfg::E, TPC = Cfg::TPC, W = Cfg::W;
+  __shared__ float2 sbuf[W][SPad<L>::size];
+
+  const int c = threadIdx.x % W;
+  const int t = threadIdx.x / W;
+  const int ncols = a.nx / 2;
+  const int col = blockIdx.x * W + c;
+  const bool valid = col < ncols;
+  const int colv = valid ? col : 0;
+  float2* sb = sbuf[c];
+
+  if (a.check_done && a.st->done) return;  // uniform: set only between launches
+
+  auto at = [&](int k) -> size_t { return (size_t)k * ncols + colv; };
+  float2 v[E];
+
+  // Partner value Z[-k] of column 0 (only meaningful where col == 0).  Every
+  // thread of CTA 0 takes part in the exchange; CTA 0 is uniform.
+  auto exchange0 = [&](float2 (&u)[E], float2 (&up)[E]) {
+#pragma unroll
+    for (int m = 0; m < E; ++m) sb[spad(t + m * TPC)] = u[m];
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const int k = t + m * TPC;
+      up[m] = sb[spad((L - k) & (L - 1))];
+    }
+    __syncthreads();
+  };
+
+  if constexpr (MODE == COL_PASS_2DF || MODE == COL_PASS_NO2DF) {
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = valid ? a.f_y[at(t + m * TPC)] : make_float2(0.f, 0.f);
+    fft_block<L, E, false>(v, sb, t, a.twy, 1);
+    const float T0 = a.st->Tf[0];
+    const float T0s = a.st->T0s[a.parity];
+    const float Tl = a.has_rf ? a.st->Tf[1] : a.st->Tf[2];  // link to the RF/PX messenger
+    const float off0 = (float)a.st->off[0];
+    float2 vp[E];
+    if (blockIdx.x == 0) exchange0(v, vp);
+    // all reads of t_2DF (including column 0's partners) before any write
+    float2 t0r[E], t0p[E];
+    if constexpr (MODE == COL_PASS_2DF) {
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        const int k = t + m * TPC;
+        t0r[m] = valid ? a.f_t0[at(k)] : make_float2(0.f, 0.f);
+        t0p[m] = (blockIdx.x == 0 && c == 0) ? a.f_t0[at((L - k) & (L - 1))] : t0r[m];
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const int k = t + m * TPC;
+      const float2 eg = valid ? a.eig[at(k)] : make_float2(1.f, 1.f);
+      if constexpr (MODE == COL_PASS_2DF) {
+        const float2 t0o = t0r[m];
+        float2 t0n, d0;
+        if (blockIdx.x == 0 && c == 0) {
+          const float2 egb = a.eig_nyq[k];
+          float2 yA, yB, tA, tB, tnA, tnB;
+          unpack_pair(v[m], vp[m], yA, yB);
+          unpack_pair(t0o, t0p[m], tA, tB);
+          const float2 dA = mode_2df(yA, tA, eg.x, eg.y, off0, Tl, T0, T0s, tnA);
+          const float2 dB = mode_2df(yB, tB, egb.x, egb.y, off0, Tl, T0, T0s, tnB);
+          d0 = repack_pair(dA, dB);
+          t0n = repack_pair(tnA, tnB);
+        } else {
+          d0 = mode_2df(v[m], t0o, eg.x, eg.y, off0, Tl, T0, T0s, t0n);
+        }
+        v[m] = d0;
+        if (valid) a.f_t0[at(k)] = t0n;
+      } else {
+        // no 1/f part: eq. (2mess_s), s = C/(C + T) y for the messenger next to s
+        if (blockIdx.x == 0 && c == 0) {
+          float2 yA, yB;
+          unpack_pair(v[m], vp[m], yA, yB);
+          const float2 egb = a.eig_nyq[k];
+          yA = cscale(yA, __fdividef(eg.x, eg.x + Tl));
+          yB = cscale(yB, __fdividef(egb.x, egb.x + Tl));
+          v[m] = repack_pair(yA, yB);
+        } else {
+          v[m] = cscale(v[m], __fdividef(eg.x, eg.x + Tl));
+        }
+      }
+    }
+    if constexpr (MODE == COL_PASS_2DF) {
+      // publish the T_0 that the new t_2DF was made with (implicit s)
+      if (blockIdx.x == 0 && threadIdx.x == 0) a.st->T0s[a.parity ^ 1] = T0;
+    }
+    fft_block<L, E, true>(v, sb, t, a.twy, 1);
+    const float sc = 1.0f / (float)L;
+    if (valid) {
+#pragma unroll
+      for (int m = 0; m < E; ++m) a.f_x[at(t + m * TPC)] = cscale(v[m], sc);
+    }
+  } else if constexpr (MODE == COL_PASS_MERGE) {
+    // Joint update of the 2DF block given the data-side messenger y (Appendix
+    // A shortcut; t_2DF marginalised): d_2DF = (C + N0) / (C + N0 + T) y, and
+    // s = C / (C + N0) d_2DF is implicit.
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = valid ? a.f_y[at(t + m * TPC)] : make_float2(0.f, 0.f);
+    fft_block<L, E, false>(v, sb, t, a.twy, 1);
+    const float Tl = a.has_rf ? a.st->Tf[1] : a.st->Tf[2];
+    const float off0 = (float)a.st->off[0];
+    float2 vp[E];
+    if (blockIdx.x == 0) exchange0(v, vp);
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const int k = t + m * TPC;
+      const float2 eg = valid ? a.eig[at(k)] : make_float2(1.f, 1.f);
+      const float pa = eg.x + eg.y + off0;          // C + N0
+      if (blockIdx.x == 0 && c == 0) {
+        const float2 egb = a.eig_nyq[k];
+        const float pb = egb.x + egb.y + off0;
+        float2 A, B;
+        unpack_pair(v[m], vp[m], A, B);
+        v[m] = repack_pair(cscale(A, __fdividef(pa, pa + Tl)), cscale(B, __fdividef(pb, pb + Tl)));
+      } else {
+        v[m] = cscale(v[m], __fdividef(pa, pa + Tl));
+      }
+    }
+    fft_block<L, E, true>(v, sb, t, a.twy, 1);
+    const float sc = 1.0f / (float)L;
+    if (valid) {
+#pragma unroll
+      for (int m = 0; m < E; ++m) a.f_x[at(t + m * TPC)] = cscale(v[m], sc);
+    }
+  } else if constexpr (MODE == COL_RESID_A) {
+    // g = S^-1 s = t0 / (C + T0) and s = C g   (2DF part present), or
+    // g = s / C with s from the stored RF field (no 1/f part)
+    float2 vp[E];
+    const float sc = 1.0f / (float)L;
+    if (a.has_f && a.merge) {
+      // s = C d0 / (C + N0), g = S^-1 s = d0 / (C + N0), from the stored d_2DF
+      const float off0 = (float)a.st->off[0];
+      float2 w[E];
+#pragma unroll
+      for (int m = 0; m < E; ++m) v[m] = valid ? a.f_x[at(t + m * TPC)] : make_float2(0.f, 0.f);
+      fft_block<L, E, false>(v, sb, t, a.twy, 1);
+      if (blockIdx.x == 0) exchange0(v, vp);
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        const int k = t + m * TPC;
+        const float2 eg = valid ? a.eig[at(k)] : make_float2(1.f, 1.f);
+        if (blockIdx.x == 0 && c == 0) {
+          const float2 egb = a.eig_nyq[k];
+          float2 A, B;
+          unpack_pair(v[m], vp[m], A, B);
+          const float2 gA = cscale(A, __fdividef(1.f, eg.x + eg.y + off0));
+          const float2 gB = cscale(B, __fdividef(1.f, egb.x + egb.y + off0));
+          v[m] = repack_pair(gA, gB);
+          w[m] = repack_pair(cscale(gA, eg.x), cscale(gB, egb.x));
+        } else {
+          const float2 g = cscale(v[m], __fdividef(1.f, eg.x + eg.y + off0));
+          v[m] = g;
+          w[m] = cscale(g, eg.x);
+        }
+      }
+      fft_block<L, E, true>(v, sb, t, a.twy, 1);
+      fft_block<L, E, true>(w, sb, t, a.twy, 1);
+      if (valid) {
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+          a.r_g[at(t + m * TPC)] = cscale(v[m], sc);
+          a.r_q[at(t + m * TPC)] = cscale(w[m], sc);
+        }
+      }
+    } else if (a.has_f) {
+#pragma unroll
+      for (int m = 0; m < E; ++m) v[m] = valid ? a.f_t0[at(t + m * TPC)] : make_float2(0.f, 0.f);
+      const float T0s = a.st->T0s[a.parity];
+      float2 w[E];
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        const int k = t + m * TPC;
+        const float2 eg = valid ? a.eig[at(k)] : make_float2(1.f, 1.f);
+        if (blockIdx.x == 0 && c == 0) {
+          const int kp = (L - k) & (L - 1);
+          const float2 egb = a.eig_nyq[k];
+          float2 A, B;
+          unpack_pair(v[m], a.f_t0[at(kp)], A, B);
+          const float ia = __fdividef(1.f, eg.x + T0s), ib = __fdividef(1.f, egb.x + T0s);
+          const float2 gA = cscale(A, ia), gB = cscale(B, ib);
+          v[m] = repack_pair(gA, gB);
+          w[m] = repack_pair(cscale(gA, eg.x), cscale(gB, egb.x));
+        } else {
+          const float2 g = cscale(v[m], __fdividef(1.f, eg.x + T0s));
+          v[m] = g;
+          w[m] = cscale(g, eg.x);
+        }
+      }
+      fft_block<L, E, true>(v, sb, t, a.twy, 1);
+      fft_block<L, E, true>(w, sb, t, a.twy, 1);
+      if (valid) {
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+          a.r_g[at(t + m * TPC)] = cscale(v[m], sc);
+          a.r_q[at(t + m * TPC)] = cscale(w[m], sc);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        v[m] = valid ? a.f_x[at(t + m * TPC)] : make_float2(0.f, 0.f);
+        if (valid) a.r_q[at(t + m * TPC)] = v[m];
+      }
+      fft_block<L, E, false>(v, sb, t, a.twy, 1);
+      if (blockIdx.x == 0) exchange0(v, vp);
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        const int k = t + m * TPC;
+        const float2 eg = valid ? a.eig[at(k)] : make_float2(1.f, 1.f);
+        if (blockIdx.x == 0 && c == 0) {
+          float2 A, B;
+          unpack_pair(v[m], vp[m], A, B);
+          v[m] = repack_pair(cscale(A, __fdividef(1.f, eg.x)), cscale(B, __fdividef(1.f, a.eig_nyq[k].x)));
+        } else {
+          v[m] = cscale(v[m], __fdividef(1.f, eg.x));
+        }
+      }
+      fft_block<L, E, true>(v, sb, t, a.twy, 1);
+      if (valid) {
+#pragma unroll
+        for (int m = 0; m < E; ++m) a.r_g[at(t + m * TPC)] = cscale(v[m], sc);
+      }
+    }
+  } else if constexpr (MODE == COL_RESID_C) {
+    // q += N_2DF g'  (the given 1/f eigenvalues)
+    float2 vp[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = valid ? a.r_g[at(t + m * TPC)] : make_float2(0.f, 0.f);
+    fft_block<L, E, false>(v, sb, t, a.twy, 1);
+    if (blockIdx.x == 0) exchange0(v, vp);
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const int k = t + m * TPC;
+      const float2 eg = valid ? a.eig[at(k)] : make_float2(0.f, 0.f);
+      if (blockIdx.x == 0 && c == 0) {
+        float2 A, B;
+        unpack_pair(v[m], vp[m], A, B);
+        v[m] = repack_pair(cscale(A, eg.y), cscale(B, a.eig_nyq[k].y));
+      } else {
+        v[m] = cscale(v[m], eg.y);
+      }
+    }
+    fft_block<L, E, true>(v, sb, t, a.twy, 1);
+    const float sc = 1.0f / (float)L;
+    if (valid) {
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        const size_t i = at(t + m * TPC);
+        const float2 q = a.r_q[i];
+        a.r_q[i] = make_float2(fmaf(v[m].x, sc, q.x), fmaf(v[m].y, sc, q.y));
+      }
+    }
+  } else if constexpr (MODE == COL_FWD || MODE == COL_INV) {
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = valid ? a.in[at(t + m * TPC)] : make_float2(0.f, 0.f);
+    fft_block<L, E, MODE == COL_INV>(v, sb, t, a.twy, 1);
+    const float sc = (MODE == COL_INV) ? 1.0f / (float)L : 1.0f;
+    if (valid) {
+#pragma unroll
+      for (int m = 0; m < E; ++m) a.out[at(t + m * TPC)] = cscale(v[m], sc);
+    }
+  }
+}
+
+template <int L>
+static int launch_col_L(int mode, const ColArgs& a, cudaStream_t s) {
+  using Cfg = ColCfg<L>;
+  const int ncols = a.nx / 2;
+  const dim3 grid((ncols + Cfg::W - 1) / Cfg::W), block(Cfg::THREADS);
+  switch (mode) {
+    case COL_PASS_2DF: col_kernel<L, COL_PASS_2DF><<<grid, block, 0, s>>>(a); break;
+    case COL_PASS_NO2DF: col_kernel<L, COL_PASS_NO2DF><<<grid, block, 0, s>>>(a); break;
+    case COL_RESID_A: col_kernel<L, COL_RESID_A><<<grid, block, 0, s>>>(a); break;
+    case COL_RESID_C: col_kernel<L, COL_RESID_C><<<grid, block, 0, s>>>(a); break;
+    case COL_FWD: col_kernel<L, COL_FWD><<<grid, block, 0, s>>>(a); break;
+    case COL_INV: col_kernel<L, COL_INV><<<grid, block, 0, s>>>(a); break;
+    case COL_PASS_MERGE: col_kernel<L, COL_PASS_MERGE><<<grid, block, 0, s>>>(a); break;
+    default: return (int)cudaErrorInvalidValue;
+  }
+  return (int)cudaGetLastError();
+}
+
+int launch_col(int mode, const ColArgs& a, cudaStream_t s) {
+  switch (a.ny) {
+    case 32: return launch_col_L<32>(mode, a, s);
+    case 64: return launch_col_L<64>(mode, a, s);
+    case 128: return launch_col_L<128>(mode, a, s);
+    case 256: return launch_col_L<256>(mode, a, s);
+    case 512: return launch_col_L<512>(mode, a, s);
+    case 1024: return launch_col_L<1024>(mode, a, s);
+    case 2048: return launch_col_L<2048>(mode, a, s);
+    case 4096: return launch_col_L<4096>(mode, a, s);
+    default: return (int)cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace wf

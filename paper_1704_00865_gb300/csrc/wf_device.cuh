@@ -1,0 +1,302 @@
+// wf_device.cuh -- device building blocks of the GB300 messenger Wiener filter:
+// complex arithmetic, register DFTs, a shared-memory Stockham FFT engine,
+// the real<->complex row-transform wrappers and the device-resident state.
+//
+// The transforms are the flat-sky stand-ins for the spherical-harmonic
+// transforms of Sec. 2 of Huffenberger 2017 (two transforms per iteration):
+// a row-wise real DFT along x (the basis where horizontal stripes are
+// diagonal) and a column DFT along y (completing the 2D DFT where the signal
+// and the 1/f noise are diagonal).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace wf {
+
+// ---------------------------------------------------------------- complex
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+// multiply by -i (forward transforms) or +i (inverse transforms)
+template <bool INV>
+__device__ __forceinline__ float2 rot90(float2 a) {
+  return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+template <bool INV>
+__device__ __forceinline__ float2 tw_dir(float2 w) { return INV ? cconj(w) : w; }
+
+// ---------------------------------------------------------------- small DFTs
+// Forward DFTs use exp(-2 pi i nk/R); INV uses exp(+2 pi i nk/R); no scaling.
+template <bool INV>
+__device__ __forceinline__ void dft2(float2& a, float2& b) {
+  float2 t = a;
+  a = cadd(t, b);
+  b = csub(t, b);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
+  float2 s02 = cadd(a0, a2), d02 = csub(a0, a2);
+  float2 s13 = cadd(a1, a3), d13 = rot90<INV>(csub(a1, a3));
+  a0 = cadd(s02, s13);
+  a2 = csub(s02, s13);
+  a1 = cadd(d02, d13);
+  a3 = csub(d02, d13);
+}
+
+// cos(pi/4), cos(pi/8), sin(pi/8)
+#define WF_C4 0.70710678118654752f
+#define WF_C8 0.92387953251128674f
+#define WF_S8 0.38268343236508977f
+
+// multiply by W8^1 = exp(-+ i pi/4)
+template <bool INV>
+__device__ __forceinline__ float2 mul_w8_1(float2 a) {
+  return INV ? make_float2(WF_C4 * (a.x - a.y), WF_C4 * (a.x + a.y))
+             : make_float2(WF_C4 * (a.x + a.y), WF_C4 * (a.y - a.x));
+}
+// multiply by W8^3 = exp(-+ 3 i pi/4)
+template <bool INV>
+__device__ __forceinline__ float2 mul_w8_3(float2 a) {
+  return INV ? make_float2(-WF_C4 * (a.x + a.y), WF_C4 * (a.x - a.y))
+             : make_float2(WF_C4 * (a.y - a.x), -WF_C4 * (a.x + a.y));
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft8(float2* a) {
+  // even / odd halves, then combine with W8^k
+  float2 e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6];
+  float2 o0 = a[1], o1 = a[3], o2 = a[5], o3 = a[7];
+  dft4<INV>(e0, e1, e2, e3);
+  dft4<INV>(o0, o1, o2, o3);
+  o1 = mul_w8_1<INV>(o1);
+  o2 = rot90<INV>(o2);
+  o3 = mul_w8_3<INV>(o3);
+  a[0] = cadd(e0, o0); a[4] = csub(e0, o0);
+  a[1] = cadd(e1, o1); a[5] = csub(e1, o1);
+  a[2] = cadd(e2, o2); a[6] = csub(e2, o2);
+  a[3] = cadd(e3, o3); a[7] = csub(e3, o3);
+}
+
+template <bool INV>
+__device__ __forceinline__ float2 w16(int m, float2 a) {
+  // multiply a by W16^m for the m that occur in the 4x4 split
+  float2 w;
+  switch (m) {
+    case 1: w = make_float2(WF_C8, -WF_S8); break;
+    case 2: w = make_float2(WF_C4, -WF_C4); break;
+    case 3: w = make_float2(WF_S8, -WF_C8); break;
+    case 4: w = make_float2(0.f, -1.f); break;
+    case 6: w = make_float2(-WF_C4, -WF_C4); break;
+    case 9: w = make_float2(-WF_C8, WF_S8); break;
+    default: return a;
+  }
+  return cmul(a, tw_dir<INV>(w));
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft16(float2* a) {
+  // 16 = 4 x 4: X[k1 + 4 k2] = sum_n2 W4^{n2 k2} W16^{n2 k1} sum_n1 a[4 n1 + n2] W4^{n1 k1}
+  float2 y[16];
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) {
+    float2 b0 = a[n2], b1 = a[n2 + 4], b2 = a[n2 + 8], b3 = a[n2 + 12];
+    dft4<INV>(b0, b1, b2, b3);
+    y[n2 * 4 + 0] = b0;
+    y[n2 * 4 + 1] = w16<INV>(n2 * 1, b1);
+    y[n2 * 4 + 2] = w16<INV>(n2 * 2, b2);
+    y[n2 * 4 + 3] = w16<INV>(n2 * 3, b3);
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    float2 c0 = y[0 * 4 + k1], c1 = y[1 * 4 + k1], c2 = y[2 * 4 + k1], c3 = y[3 * 4 + k1];
+    dft4<INV>(c0, c1, c2, c3);
+    a[k1] = c0; a[k1 + 4] = c1; a[k1 + 8] = c2; a[k1 + 12] = c3;
+  }
+}
+
+template <int R, bool INV>
+__device__ __forceinline__ void dftR(float2* u) {
+  if constexpr (R == 2) dft2<INV>(u[0], u[1]);
+  else if constexpr (R == 4) dft4<INV>(u[0], u[1], u[2], u[3]);
+  else if constexpr (R == 8) dft8<INV>(u);
+  else if constexpr (R == 16) dft16<INV>(u);
+}
+
+// ---------------------------------------------------------------- FFT engine
+// Shared-memory index padding: one extra slot every 16 complex values, so the
+// strided scatters of the early Stockham stages do not pile onto one bank.
+__device__ __forceinline__ int spad(int i) { return i + (i >> 4); }
+template <int L>
+struct SPad { static constexpr int size = L + L / 16; };
+
+// Radix of the stage that starts with sub-transform length NS.
+template <int L, int E, int NS>
+struct StageRadix {
+  static constexpr int rem = L / NS;
+  static constexpr int value = rem >= E ? E : rem;
+};
+
+// One Stockham autosort stage (radix R, sub-transform length NS) of a
+// length-L complex DFT computed by TPF = L/E threads, E values per thread.
+// Inputs are the "natural" layout (thread t holds x[t + m*TPF], m =
+// b + r*(E/R)); outputs go to shared memory at their autosort positions, or,
+// for the last stage, back to the registers in the natural layout.
+// twtab holds exp(-2 pi i k / (L*twstride)), k < L*twstride.
+template <int L, int E, int NS, bool INV>
+struct FFTStages {
+  static __device__ __forceinline__ void run(float2 (&v)[E], float2* sb, int t,
+                                             const float2* __restrict__ twtab, int twstride) {
+    constexpr int R = StageRadix<L, E, NS>::value;
+    constexpr int TPF = L / E;
+    constexpr int B = E / R;
+    constexpr bool LAST = (NS * R == L);
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int j = t + b * TPF;
+      const int jm = j & (NS - 1);
+      float2 u[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) u[r] = v[b + r * B];
+      if constexpr (NS > 1) {
+        // twiddles W_{NS R}^{jm r}: exact table values every 4th power,
+        // products in between (at most 3 multiplications deep)
+        const int step = jm * (L / (NS * R)) * twstride;
+        float2 w1 = tw_dir<INV>(__ldg(&twtab[step]));
+        float2 wr = w1;
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          if ((r & 3) == 0) wr = tw_dir<INV>(__ldg(&twtab[step * r]));
+          u[r] = cmul(u[r], wr);
+          wr = cmul(wr, w1);
+        }
+      }
+      dftR<R, INV>(u);
+      if constexpr (LAST) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[b + r * B] = u[r];
+      } else {
+        const int base = (j - jm) * R + jm;
+#pragma unroll
+        for (int r = 0; r < R; ++r) sb[spad(base + r * NS)] = u[r];
+      }
+    }
+    if constexpr (!LAST) {
+      __syncthreads();
+#pragma unroll
+      for (int m = 0; m < E; ++m) v[m] = sb[spad(t + m * TPF)];
+      __syncthreads();
+      FFTStages<L, E, NS * R, INV>::run(v, sb, t, twtab, twstride);
+    }
+  }
+};
+
+// Full complex DFT of length L (no scaling).  Every thread of the block must
+// call it (it contains __syncthreads); sb is this transform's own padded
+// shared buffer of SPad<L>::size values.
+template <int L, int E, bool INV>
+__device__ __forceinline__ void fft_block(float2 (&v)[E], float2* sb, int t,
+                                          const float2* __restrict__ twtab, int twstride) {
+  FFTStages<L, E, 1, INV>::run(v, sb, t, twtab, twstride);
+}
+
+// ---------------------------------------------------------------- real rows
+// Real length-N rows (N = 2M) through complex length-M transforms:
+// z[n] = x[2n] + i x[2n+1].  The packed half spectrum holds X[k] at k = 1..M-1
+// and (X[0], X[M]) -- both real -- as the pair in slot 0.
+
+// Before an inverse complex FFT: X (natural layout in v) -> Z so that
+// IFFT_M(Z) / M gives z.  Here the 1/N scaling of the inverse real DFT is
+// folded in.  twx = exp(-2 pi i k / N).
+template <int M, int E>
+__device__ __forceinline__ void c2r_pre(float2 (&v)[E], float2* sb, int t,
+                                        const float2* __restrict__ twx) {
+  constexpr int TPF = M / E;
+  const float s = 0.5f / (float)M;  // 1/(2M) = 1/N, times the 1/2 of E and O
+#pragma unroll
+  for (int m = 0; m < E; ++m) sb[spad(t + m * TPF)] = v[m];
+  __syncthreads();
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const int k = t + m * TPF;
+    float2 X = v[m];
+    if (k == 0) {
+      v[m] = make_float2((X.x + X.y) * s * 1.0f, (X.x - X.y) * s);
+    } else {
+      float2 Xm = cconj(sb[spad(M - k)]);
+      float2 Ek = cadd(X, Xm);
+      float2 Ok = cmul(csub(X, Xm), cconj(__ldg(&twx[k])));
+      // Z = E + i O
+      v[m] = make_float2((Ek.x - Ok.y) * s, (Ek.y + Ok.x) * s);
+    }
+  }
+  __syncthreads();
+}
+
+// After a forward complex FFT: Z (natural layout) -> packed X.
+template <int M, int E>
+__device__ __forceinline__ void r2c_post(float2 (&v)[E], float2* sb, int t,
+                                         const float2* __restrict__ twx) {
+  constexpr int TPF = M / E;
+#pragma unroll
+  for (int m = 0; m < E; ++m) sb[spad(t + m * TPF)] = v[m];
+  __syncthreads();
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const int k = t + m * TPF;
+    float2 Z = v[m];
+    if (k == 0) {
+      v[m] = make_float2(Z.x + Z.y, Z.x - Z.y);
+    } else {
+      float2 Zm = cconj(sb[spad(M - k)]);
+      float2 Ek = cscale(cadd(Z, Zm), 0.5f);
+      float2 D = cscale(csub(Z, Zm), 0.5f);
+      float2 Ok = make_float2(D.y, -D.x);  // D / i
+      v[m] = cadd(Ek, cmul(__ldg(&twx[k]), Ok));
+    }
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------- state
+// Device-resident solver state.  Problem constants are written by the setup
+// kernels; lambda and the derived messenger covariances by the controller.
+struct WfState {
+  // problem constants
+  double tau[3];      // tau_i for parts 2DF, RF, PX (0 when absent)
+  double off[3];      // Nbar_i = (given eigenvalue) + off_i  (moved white - tau)
+  double var_shift;   // N_PX used for the residual: nbar_px - off[2]
+  double du2;         // ||d_unmasked||^2
+  double min_v, min_f, min_s, min_a2;
+  unsigned err;       // setup validation bits (WF_ERR_*)
+  int n_unmasked;
+  // cooling / control
+  double lam;         // current lambda
+  float Tf[3];        // lambda * tau_i as float
+  float T0s[2];       // T_0 with which the stored t_0 was made, by parity slot
+  double prev_rho2;   // adaptive rule reference (< 0: none)
+  double rho2, gm2, g2, rel_u, rel_m;
+  int done;           // 1: stop (converged or out of iterations)
+  int status;         // WF_OK / WF_ENOCONV
+  int iter;           // iterations completed in this run
+  int checkpoints;
+  int level, in_level;
+  int pad_[2];
+};
+
+enum : unsigned {
+  WF_ERR_D_NONFINITE = 1u, WF_ERR_VAR = 2u, WF_ERR_C = 4u, WF_ERR_P1F = 8u,
+  WF_ERR_PST = 16u, WF_ERR_A2 = 32u, WF_ERR_ASYM = 64u, WF_ERR_ALLMASKED = 128u
+};
+
+// Every messenger update has the form x = (B a + A b)/(A + B): the mean of x
+// under the Gaussian terms (x-a)^2/A + (x-b)^2/B, i.e. the
+// (A^-1 + B^-1)^-1 (A^-1 a + B^-1 b) of eqs. (ew_t), (2mess_t1)-(2mess_t0).
+__device__ __forceinline__ float link_w(float A, float B) { return __fdividef(B, A + B); }
+
+}  // namespace wf

@@ -1,0 +1,127 @@
+// wf_internal.h -- kernel argument blocks and launchers shared between the
+// translation units of libwf (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace wf {
+
+struct WfState;
+
+// Row-pass modes (one CTA handles ROWS map rows; each row is one real DFT).
+enum RowMode : int {
+  ROW_PASS_RF = 0,    // t_PX update between the row transforms, then d_RF, t_RF
+  ROW_PASS_NORF = 1,  // t_PX update only (no stripe part); writes t_PX in RF
+  ROW_RESID_B = 2,    // residual: g, s to pixels; N_PX g' + s - d; N_RF g'
+  ROW_RESID_D = 3,    // residual: Delta d to pixels; ||rho_u||^2
+  ROW_C2R = 4,        // RF -> pixel (export)
+  ROW_R2C = 5,        // pixel -> RF
+  ROW_NMODES = 6
+};
+
+// Column-pass modes (one CTA handles W complex columns of length ny).
+enum ColMode : int {
+  COL_PASS_2DF = 0,   // d_2DF, t_2DF updates between the column transforms
+  COL_PASS_NO2DF = 1, // s update only (no 1/f part); writes s in RF
+  COL_RESID_A = 2,    // residual: g = S^-1 s and s, to RF
+  COL_RESID_C = 3,    // residual: add N_2DF g' (in RF)
+  COL_FWD = 4,        // RF -> 2D Fourier
+  COL_INV = 5,        // 2D Fourier -> RF (with 1/ny)
+  COL_PASS_MERGE = 6, // joint (s, t_2DF, d_2DF) update given the RF messenger
+  COL_NMODES = 7
+};
+
+struct RowArgs {
+  int ny, nx;
+  int has_rf;                 // stripe part present
+  int check_done;             // return at once when the solver is done
+  const float4* dn;           // [ny][nx/2] pixel pairs (d0, nb0, d1, nb1); nb < 0 = masked
+  float2* f_d1;               // RF fields [ny][nx/2]
+  float2* f_t1;
+  const float2* f_x;          // signal-side neighbour in RF (d_2DF or s)
+  float2* f_y;                // t_PX in RF (no stripe part)
+  const float* pst;           // [nx/2+1] stripe eigenvalues
+  const float* a2;            // [ny] a(y)^2 or nullptr
+  const float2* twx;          // exp(-2 pi i k/nx), k < nx
+  WfState* st;
+  float2* r_g;                // residual scratch (RF)
+  float2* r_q;
+  double* part0;              // per-CTA partial sums
+  double* part1;
+  const float2* in_rf;        // generic transforms
+  float2* out_rf;
+  const float2* in_px;        // pixel pairs
+  float2* out_px;
+};
+
+struct ColArgs {
+  int ny, nx;
+  int has_rf, has_f;
+  int merge;                  // 2DF block updated jointly (no stored t_2DF)
+  int check_done;             // return at once when the solver is done
+  int parity;                 // slot of T0s holding the stored t_2DF's T_0
+  const float2* f_y;          // data-side messenger in RF (t_RF or t_PX)
+  float2* f_x;                // output in RF (d_2DF or s)
+  float2* f_t0;               // t_2DF [ny][nx/2] (2D Fourier)
+  const float2* eig;          // [ny][nx/2] (C, P1f) for kx = col
+  const float2* eig_nyq;      // [ny] (C, P1f) at kx = nx/2
+  const float2* twy;          // exp(-2 pi i k/ny), k < ny
+  WfState* st;
+  float2* r_g;
+  float2* r_q;
+  const float2* in;           // generic transforms
+  float2* out;
+};
+
+// launchers (return a cudaError_t as int)
+int launch_row(int mode, const RowArgs& a, cudaStream_t s);
+int launch_col(int mode, const ColArgs& a, cudaStream_t s);
+int row_grid(int nx, int ny);  // CTAs of a row pass (size of partial-sum arrays)
+bool size_supported(int n);
+
+// setup / control kernels
+struct SetupArgs {
+  int ny, nx;
+  const float* d;
+  const float* var;
+  const uint8_t* mask;
+  const float* C;
+  const float* P1f;
+  const float* Pst;
+  const float* a2;
+  float4* dn;
+  float2* eig;
+  float2* eig_nyq;
+  float* pst;
+  float* a2_out;
+  double* part;               // scratch for partial minima / sums
+  WfState* st;
+  double theta[3];
+  double split_f, split_w;
+  int has_rf, has_f;
+  int merge;
+};
+int launch_setup(const SetupArgs& a, cudaStream_t s);
+
+struct CtrlArgs {
+  WfState* st;
+  const double* part_g;       // [nrow] (gm2, g2) partials from ROW_RESID_B
+  const double* part_g2;
+  const double* part_rho;     // [nrow] rho^2 partials from ROW_RESID_D
+  int nrow;
+  int R;
+  int max_iters;
+  double tol;
+  double tol_u;
+  int mode;                   // 0 fixed, 1 adaptive
+  const double* lam_sched;    // fixed: device arrays
+  const int* it_sched;
+  int nlevels;
+  double ratio, expo, snap;
+  int count_iters;            // add R to iter (0 for a residual-only call)
+};
+int launch_ctrl(const CtrlArgs& a, cudaStream_t s);
+int launch_set_lambda(WfState* st, double lam, int reset, cudaStream_t s);
+
+}  // namespace wf

@@ -1,0 +1,273 @@
+// wf_rows.cu -- the row pass of the messenger iteration and the row steps of
+// the residual (Huffenberger 2017, Sec. 2).
+//
+// One CTA owns ROWS map rows; each row is a real length-nx signal handled by
+// TPF = (nx/2)/E threads through a complex length-nx/2 Stockham FFT in
+// shared memory.  The pixel-space messenger update (eq. 2mess_t1 analogue:
+// white noise and mask, diagonal in pixels) sits between the inverse and the
+// forward row transform, and the stripe-basis updates (eqs. 2mess_d0 and
+// 2mess_t0 analogues: stripe noise, diagonal in the row-wise DFT) follow the
+// forward transform, so a row is read and written once per iteration.
+#include "wf_device.cuh"
+#include "wf_internal.h"
+
+namespace wf {
+
+template <int M>
+struct RowCfg {
+  static constexpr int E = (M >= 2048) ? 16 : 8;
+  static constexpr int TPF = M / E;
+  static constexpr int ROWS = (256 / TPF) >= 1 ? (256 / TPF) : 1;
+  static constexpr int THREADS = ROWS * TPF;
+};
+
+// deterministic block sum of one double per thread (fixed tree)
+template <int THREADS>
+__device__ __forceinline__ double block_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  constexpr int NW = (THREADS + 31) / 32;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < NW; ++i) s += red[i];
+  }
+  return s;
+}
+
+// t_PX update for one pixel: links Nbar_PX to d and T_PX to u (the field on
+// the signal side); masked pixels (nb < 0, i.e. Nbar = inf) take u.
+__device__ __forceinline__ float tpx_update(float d, float nb, float u, float T2) {
+  return nb < 0.f ? u : __fdividef(fmaf(T2, d, nb * u), nb + T2);
+}
+
+template <int M, int MODE>
+__global__ void __launch_bounds__(RowCfg<M>::THREADS)
+row_kernel(RowArgs a) {
+  using Cfg = RowCfg<M>;
+  constexpr int E = Cfg::E, TPF = Cfg::TPF, ROWS = Cfg::ROWS;
+  __shared__ float2 sbuf[ROWS][SPad<M>::size];
+  __shared__ double red[(Cfg::THREADS + 31) / 32];
+
+  const int g = threadIdx.x / TPF;
+  const int t = threadIdx.x - g * TPF;
+  const int y = blockIdx.x * ROWS + g;
+  const bool valid = y < a.ny;
+  const size_t row0 = (size_t)(valid ? y : 0) * M;
+  float2* sb = sbuf[g];
+
+  if (a.check_done && a.st->done) return;  // uniform: set only between launches
+
+  float2 v[E];
+
+  if constexpr (MODE == ROW_PASS_RF || MODE == ROW_PASS_NORF) {
+    const float T2 = a.st->Tf[2];
+    // field on the signal side of t_PX: d_RF (stripe part) or the RF input
+    const float2* src = (MODE == ROW_PASS_RF) ? a.f_d1 : a.f_x;
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = valid ? src[row0 + t + m * TPF] : make_float2(0.f, 0.f);
+    c2r_pre<M, E>(v, sb, t, a.twx);
+    fft_block<M, E, true>(v, sb, t, a.twx, 2);
+    // eq. (2mess_t1) analogue in pixel space, two pixels per complex value
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const float4 q = valid ? a.dn[row0 + t + m * TPF] : make_float4(0.f, -1.f, 0.f, -1.f);
+      v[m] = make_float2(tpx_update(q.x, q.y, v[m].x, T2), tpx_update(q.z, q.w, v[m].y, T2));
+    }
+    fft_block<M, E, false>(v, sb, t, a.twx, 2);
+    r2c_post<M, E>(v, sb, t, a.twx);
+    if constexpr (MODE == ROW_PASS_NORF) {
+      if (valid) {
+#pragma unroll
+        for (int m = 0; m < E; ++m) a.f_y[row0 + t + m * TPF] = v[m];
+      }
+    } else {
+      // eqs. (2mess_d0), (2mess_t0) analogues in the stripe basis
+      const float T1 = a.st->Tf[1];
+      const float off1 = (float)a.st->off[1];
+      const float a2y = (a.a2 != nullptr && valid) ? a.a2[y] : 1.f;
+      if (valid) {
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+          const int k = t + m * TPF;
+          const float2 t1o = a.f_t1[row0 + k];
+          const float2 xo = a.f_x[row0 + k];
+          const float2 t2 = v[m];
+          float2 d1, t1;
+          if (k == 0) {  // packed (kx = 0, kx = M) real pair
+            const float nr = fmaf(a2y, a.pst[0], off1), ni = fmaf(a2y, a.pst[M], off1);
+            d1.x = __fdividef(fmaf(nr, t2.x, T2 * t1o.x), nr + T2);
+            d1.y = __fdividef(fmaf(ni, t2.y, T2 * t1o.y), ni + T2);
+            t1.x = __fdividef(fmaf(T1, d1.x, nr * xo.x), nr + T1);
+            t1.y = __fdividef(fmaf(T1, d1.y, ni * xo.y), ni + T1);
+          } else {
+            const float nb = fmaf(a2y, a.pst[k], off1);
+            const float wa = __fdividef(nb, nb + T2);      // weight of t_PX
+            d1 = make_float2(fmaf(wa, t2.x - t1o.x, t1o.x), fmaf(wa, t2.y - t1o.y, t1o.y));
+            const float wb = __fdividef(nb, nb + T1);      // weight of x
+            t1 = make_float2(fmaf(wb, xo.x - d1.x, d1.x), fmaf(wb, xo.y - d1.y, d1.y));
+          }
+          a.f_d1[row0 + k] = d1;
+          a.f_t1[row0 + k] = t1;
+        }
+      }
+    }
+  } else if constexpr (MODE == ROW_RESID_B) {
+    // g = S^-1 s and s arrive in RF; go to pixels.
+    float2 w[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      v[m] = valid ? a.r_g[row0 + t + m * TPF] : make_float2(0.f, 0.f);
+      w[m] = valid ? a.r_q[row0 + t + m * TPF] : make_float2(0.f, 0.f);
+    }
+    c2r_pre<M, E>(v, sb, t, a.twx);
+    fft_block<M, E, true>(v, sb, t, a.twx, 2);
+    c2r_pre<M, E>(w, sb, t, a.twx);
+    fft_block<M, E, true>(w, sb, t, a.twx, 2);
+    const float vshift = (float)a.st->var_shift;
+    double gm2 = 0.0, g2 = 0.0;
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const float4 q = valid ? a.dn[row0 + t + m * TPF] : make_float4(0.f, -1.f, 0.f, -1.f);
+      float gp[2], qp[2];
+      const float gv[2] = {v[m].x, v[m].y}, sv[2] = {w[m].x, w[m].y};
+      const float dv[2] = {q.x, q.z}, nv[2] = {q.y, q.w};
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const double gd = (double)gv[h];
+        if (valid) g2 += gd * gd;
+        if (nv[h] < 0.f) {  // masked: the residual there is g itself
+          if (valid) gm2 += gd * gd;
+          gp[h] = 0.f;
+          qp[h] = 0.f;
+        } else {             // N_PX g' + s - d with the full pixel variance
+          gp[h] = gv[h];
+          qp[h] = fmaf(nv[h] + vshift, gv[h], sv[h] - dv[h]);
+        }
+      }
+      v[m] = make_float2(gp[0], gp[1]);
+      w[m] = make_float2(qp[0], qp[1]);
+    }
+    fft_block<M, E, false>(v, sb, t, a.twx, 2);
+    r2c_post<M, E>(v, sb, t, a.twx);
+    fft_block<M, E, false>(w, sb, t, a.twx, 2);
+    r2c_post<M, E>(w, sb, t, a.twx);
+    if (valid) {
+      const float a2y = (a.a2 != nullptr) ? a.a2[y] : 1.f;
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        const int k = t + m * TPF;
+        float2 q = w[m];
+        if (a.has_rf) {  // + N_RF g' with the given stripe eigenvalues
+          if (k == 0) {
+            q.x = fmaf(a2y * a.pst[0], v[m].x, q.x);
+            q.y = fmaf(a2y * a.pst[M], v[m].y, q.y);
+          } else {
+            const float n1 = a2y * a.pst[k];
+            q = make_float2(fmaf(n1, v[m].x, q.x), fmaf(n1, v[m].y, q.y));
+          }
+        }
+        a.r_g[row0 + k] = v[m];
+        a.r_q[row0 + k] = q;
+      }
+    }
+    double s0 = block_sum<Cfg::THREADS>(gm2, red);
+    double s1 = block_sum<Cfg::THREADS>(g2, red);
+    if (threadIdx.x == 0) {
+      a.part0[blockIdx.x] = s0;
+      a.part1[blockIdx.x] = s1;
+    }
+  } else if constexpr (MODE == ROW_RESID_D) {
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = valid ? a.r_q[row0 + t + m * TPF] : make_float2(0.f, 0.f);
+    c2r_pre<M, E>(v, sb, t, a.twx);
+    fft_block<M, E, true>(v, sb, t, a.twx, 2);
+    double r2 = 0.0;
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const float4 q = valid ? a.dn[row0 + t + m * TPF] : make_float4(0.f, -1.f, 0.f, -1.f);
+      if (valid) {
+        if (q.y >= 0.f) r2 += (double)v[m].x * (double)v[m].x;
+        if (q.w >= 0.f) r2 += (double)v[m].y * (double)v[m].y;
+      }
+    }
+    double s0 = block_sum<Cfg::THREADS>(r2, red);
+    if (threadIdx.x == 0) a.part0[blockIdx.x] = s0;
+  } else if constexpr (MODE == ROW_C2R) {
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = valid ? a.in_rf[row0 + t + m * TPF] : make_float2(0.f, 0.f);
+    c2r_pre<M, E>(v, sb, t, a.twx);
+    fft_block<M, E, true>(v, sb, t, a.twx, 2);
+    if (valid) {
+#pragma unroll
+      for (int m = 0; m < E; ++m) a.out_px[row0 + t + m * TPF] = v[m];
+    }
+  } else if constexpr (MODE == ROW_R2C) {
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = valid ? a.in_px[row0 + t + m * TPF] : make_float2(0.f, 0.f);
+    fft_block<M, E, false>(v, sb, t, a.twx, 2);
+    r2c_post<M, E>(v, sb, t, a.twx);
+    if (valid) {
+#pragma unroll
+      for (int m = 0; m < E; ++m) a.out_rf[row0 + t + m * TPF] = v[m];
+    }
+  }
+}
+
+template <int M>
+static int launch_row_M(int mode, const RowArgs& a, cudaStream_t s) {
+  using Cfg = RowCfg<M>;
+  const dim3 grid((a.ny + Cfg::ROWS - 1) / Cfg::ROWS), block(Cfg::THREADS);
+  switch (mode) {
+    case ROW_PASS_RF: row_kernel<M, ROW_PASS_RF><<<grid, block, 0, s>>>(a); break;
+    case ROW_PASS_NORF: row_kernel<M, ROW_PASS_NORF><<<grid, block, 0, s>>>(a); break;
+    case ROW_RESID_B: row_kernel<M, ROW_RESID_B><<<grid, block, 0, s>>>(a); break;
+    case ROW_RESID_D: row_kernel<M, ROW_RESID_D><<<grid, block, 0, s>>>(a); break;
+    case ROW_C2R: row_kernel<M, ROW_C2R><<<grid, block, 0, s>>>(a); break;
+    case ROW_R2C: row_kernel<M, ROW_R2C><<<grid, block, 0, s>>>(a); break;
+    default: return (int)cudaErrorInvalidValue;
+  }
+  return (int)cudaGetLastError();
+}
+
+int launch_row(int mode, const RowArgs& a, cudaStream_t s) {
+  switch (a.nx / 2) {
+    case 16: return launch_row_M<16>(mode, a, s);
+    case 32: return launch_row_M<32>(mode, a, s);
+    case 64: return launch_row_M<64>(mode, a, s);
+    case 128: return launch_row_M<128>(mode, a, s);
+    case 256: return launch_row_M<256>(mode, a, s);
+    case 512: return launch_row_M<512>(mode, a, s);
+    case 1024: return launch_row_M<1024>(mode, a, s);
+    case 2048: return launch_row_M<2048>(mode, a, s);
+    default: return (int)cudaErrorInvalidValue;
+  }
+}
+
+template <int M>
+static int rows_per_cta() { return RowCfg<M>::ROWS; }
+
+int row_grid(int nx, int ny) {
+  int r = 1;
+  switch (nx / 2) {
+    case 16: r = rows_per_cta<16>(); break;
+    case 32: r = rows_per_cta<32>(); break;
+    case 64: r = rows_per_cta<64>(); break;
+    case 128: r = rows_per_cta<128>(); break;
+    case 256: r = rows_per_cta<256>(); break;
+    case 512: r = rows_per_cta<512>(); break;
+    case 1024: r = rows_per_cta<1024>(); break;
+    case 2048: r = rows_per_cta<2048>(); break;
+    default: r = 1;
+  }
+  return (ny + r - 1) / r;
+}
+
+bool size_supported(int n) {
+  return n >= 32 && n <= 4096 && (n & (n - 1)) == 0;
+}
+
+}  // namespace wf

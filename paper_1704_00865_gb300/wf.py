@@ -1,0 +1,308 @@
+"""Thin ctypes binding of libwf.so (C ABI in include/wf.h).
+
+Argument marshalling only: every step of the Wiener-filter iteration runs in
+the library's CUDA kernels.  Arrays may be torch tensors (CUDA or CPU) or
+numpy arrays; CPU arrays are handed to the library as host pointers and the
+library stages them.  There is no fallback: if libwf.so is missing this
+module raises.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+WF_OK, WF_EINVAL, WF_ENOTPD, WF_ENOCONV, WF_ETIMEOUT, WF_ECUDA, WF_ENOMEM, WF_EUNSUPPORTED = range(8)
+WF_PART_WHITE, WF_PART_1F, WF_PART_STRIPE = 1, 2, 4
+WF_SCHED_FIXED, WF_SCHED_ADAPTIVE = 0, 1
+WF_FIELD_S, WF_FIELD_T_2DF, WF_FIELD_D_2DF, WF_FIELD_T_RF, WF_FIELD_D_RF = range(5)
+
+# every symbol include/wf.h declares
+EXPORTS = ["wf_version", "wf_strerror", "wf_params_default", "wf_plan_create", "wf_plan_destroy",
+           "wf_set_problem", "wf_run", "wf_iterate", "wf_residual", "wf_get_field", "wf_solve",
+           "wf_fft2", "wf_launch_count", "wf_time_passes"]
+
+
+class wf_schedule(C.Structure):
+    _fields_ = [("mode", C.c_int), ("lam", C.POINTER(C.c_double)), ("iters", C.POINTER(C.c_int)),
+                ("nlevels", C.c_int), ("lam0", C.c_double), ("ratio", C.c_double),
+                ("expo", C.c_double), ("snap", C.c_double)]
+
+
+class wf_params(C.Structure):
+    _fields_ = [("theta", C.c_double * 3), ("split_f", C.c_double), ("split_w", C.c_double),
+                ("tol_u_scale", C.c_double), ("residual_every", C.c_int), ("max_iters", C.c_int),
+                ("check_every", C.c_int), ("merge_2df", C.c_int), ("reserved", C.c_int * 4)]
+
+
+class wf_stats(C.Structure):
+    _fields_ = [("iters", C.c_int), ("checkpoints", C.c_int), ("lam_final", C.c_double),
+                ("rel_rho_u", C.c_double), ("rel_rho_m", C.c_double), ("tau", C.c_double * 3),
+                ("status", C.c_int), ("parts", C.c_int)]
+
+    def as_dict(self):
+        return dict(iters=self.iters, checkpoints=self.checkpoints, lam_final=self.lam_final,
+                    rel_rho_u=self.rel_rho_u, rel_rho_m=self.rel_rho_m, tau=list(self.tau),
+                    status=self.status, parts=self.parts)
+
+
+class WFError(RuntimeError):
+    def __init__(self, code, where=""):
+        self.code = code
+        super().__init__(f"{where}: {strerror(code)} (code {code})")
+
+
+_LIB = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(path: Optional[str] = None):
+    """Load libwf.so (built in-tree by paper_1704_00865_gb300.build)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    p = path or lib_path()
+    if not os.path.exists(p):
+        raise RuntimeError(f"libwf.so not found at {p}: run paper_1704_00865_gb300.build.build()")
+    L = C.CDLL(p)
+    vp = C.c_void_p
+    L.wf_version.restype = C.c_int
+    L.wf_strerror.restype = C.c_char_p
+    L.wf_strerror.argtypes = [C.c_int]
+    L.wf_params_default.restype = None
+    L.wf_params_default.argtypes = [C.POINTER(wf_params)]
+    L.wf_plan_create.argtypes = [C.POINTER(vp), C.c_int, C.c_int, C.c_uint, C.POINTER(wf_params), vp]
+    L.wf_plan_destroy.restype = None
+    L.wf_plan_destroy.argtypes = [vp]
+    L.wf_set_problem.argtypes = [vp] + [vp] * 7
+    L.wf_run.argtypes = [vp, C.POINTER(wf_schedule), C.c_double, C.POINTER(wf_stats)]
+    L.wf_iterate.argtypes = [vp, C.c_double, C.c_int]
+    L.wf_residual.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    L.wf_get_field.argtypes = [vp, C.c_int, vp]
+    L.wf_solve.argtypes = [vp] + [vp] * 7 + [C.POINTER(wf_schedule), C.c_double, vp, C.POINTER(wf_stats)]
+    L.wf_fft2.argtypes = [vp, vp, vp, C.c_int, C.c_int]
+    L.wf_launch_count.argtypes = [vp]
+    L.wf_time_passes.argtypes = [vp, C.c_double, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    for n in EXPORTS:
+        if n not in ("wf_strerror", "wf_params_default", "wf_plan_destroy", "wf_launch_count"):
+            getattr(L, n).restype = C.c_int
+    L.wf_launch_count.restype = C.c_longlong
+    _LIB = L
+    return L
+
+
+def strerror(code: int) -> str:
+    return load().wf_strerror(int(code)).decode()
+
+
+def _check(code, where):
+    if code != WF_OK:
+        raise WFError(code, where)
+
+
+def _ptr(a, dtype, n: Optional[int] = None, writable: bool = False):
+    """(pointer, keepalive) for a torch tensor or numpy array."""
+    if a is None:
+        return None, None
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            tdt = {np.float32: torch.float32, np.uint8: torch.uint8}[dtype]
+            if a.dtype != tdt or not a.is_contiguous():
+                if writable:
+                    raise ValueError("output tensor must be contiguous with the right dtype")
+                a = a.to(tdt).contiguous()
+            if n is not None and a.numel() != n:
+                raise ValueError(f"expected {n} elements, got {a.numel()}")
+            return C.c_void_p(a.data_ptr()), a
+    except ImportError:  # pragma: no cover
+        pass
+    arr = np.asarray(a)
+    if arr.dtype != dtype or not arr.flags.c_contiguous:
+        if writable:
+            raise ValueError("output array must be C-contiguous with the right dtype")
+        arr = np.ascontiguousarray(arr, dtype=dtype)
+    if n is not None and arr.size != n:
+        raise ValueError(f"expected {n} elements, got {arr.size}")
+    return C.c_void_p(arr.ctypes.data), arr
+
+
+def wf_params_default() -> wf_params:
+    p = wf_params()
+    load().wf_params_default(C.byref(p))
+    return p
+
+
+def make_params(theta=None, split_f=None, split_w=None, residual_every=None, max_iters=None,
+                check_every=None, merge_2df=None, tol_u_scale=None) -> wf_params:
+    p = wf_params_default()
+    if merge_2df is not None:
+        p.merge_2df = int(bool(merge_2df))
+    if tol_u_scale is not None:
+        p.tol_u_scale = float(tol_u_scale)
+    if theta is not None:
+        for i in range(3):
+            p.theta[i] = float(theta[i])
+    if split_f is not None:
+        p.split_f = float(split_f)
+    if split_w is not None:
+        p.split_w = float(split_w)
+    if residual_every is not None:
+        p.residual_every = int(residual_every)
+    if max_iters is not None:
+        p.max_iters = int(max_iters)
+    if check_every is not None:
+        p.check_every = int(check_every)
+    return p
+
+
+def make_schedule(mode="adaptive", lam: Sequence[float] = (), iters: Sequence[int] = (),
+                  lam0=5e5, ratio=1e-2, expo=0.7, snap=1.01):
+    s = wf_schedule()
+    keep = []
+    if mode in ("fixed", WF_SCHED_FIXED):
+        la = (C.c_double * len(lam))(*lam)
+        it = (C.c_int * len(iters))(*iters)
+        keep = [la, it]
+        s.mode = WF_SCHED_FIXED
+        s.lam = C.cast(la, C.POINTER(C.c_double))
+        s.iters = C.cast(it, C.POINTER(C.c_int))
+        s.nlevels = len(lam)
+    else:
+        s.mode = WF_SCHED_ADAPTIVE
+        s.lam0, s.ratio, s.expo, s.snap = lam0, ratio, expo, snap
+    s._keep = keep
+    return s
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except Exception:  # pragma: no cover
+        pass
+    return C.c_void_p(0)
+
+
+def wf_plan_create(ny, nx, parts, params: Optional[wf_params] = None, stream=None):
+    h = C.c_void_p()
+    p = C.byref(params) if params is not None else None
+    _check(load().wf_plan_create(C.byref(h), int(ny), int(nx), int(parts), p,
+                                 stream if stream is not None else _current_stream()), "wf_plan_create")
+    return h
+
+
+class Plan:
+    """A plan for ny x nx maps (see wf_plan_create in include/wf.h)."""
+
+    def __init__(self, ny, nx, parts=WF_PART_WHITE | WF_PART_1F | WF_PART_STRIPE,
+                 params: Optional[wf_params] = None, stream=None):
+        self.ny, self.nx, self.parts = int(ny), int(nx), int(parts)
+        self.params = params if params is not None else wf_params_default()
+        self.h = wf_plan_create(ny, nx, parts, self.params, stream)
+        self._keep = []
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            load().wf_plan_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- marshalling helpers
+    def _problem_ptrs(self, d, pixel_var, mask, Cs, P1f, Pst, amp2):
+        ny, nx = self.ny, self.nx
+        nspec = ny * (nx // 2 + 1)
+        out = [
+            _ptr(d, np.float32, ny * nx), _ptr(pixel_var, np.float32, ny * nx),
+            _ptr(mask, np.uint8, ny * nx), _ptr(Cs, np.float32, nspec),
+            _ptr(P1f, np.float32, nspec), _ptr(Pst, np.float32, nx // 2 + 1),
+            _ptr(amp2, np.float32, ny),
+        ]
+        self._keep = [k for _, k in out]
+        return [p for p, _ in out]
+
+    def set_problem(self, d, pixel_var, mask, Cs, P1f=None, Pst=None, stripe_amp2=None):
+        ptrs = self._problem_ptrs(d, pixel_var, mask, Cs, P1f, Pst, stripe_amp2)
+        _check(load().wf_set_problem(self.h, *ptrs), "wf_set_problem")
+
+    def run(self, schedule, tol: float):
+        st = wf_stats()
+        rc = load().wf_run(self.h, C.byref(schedule), float(tol), C.byref(st))
+        if rc not in (WF_OK, WF_ENOCONV):
+            _check(rc, "wf_run")
+        return st.as_dict()
+
+    def iterate(self, lam: float, n: int):
+        _check(load().wf_iterate(self.h, float(lam), int(n)), "wf_iterate")
+
+    def residual(self):
+        u, m = C.c_double(), C.c_double()
+        _check(load().wf_residual(self.h, C.byref(u), C.byref(m)), "wf_residual")
+        return u.value, m.value
+
+    def get_field(self, field: int, out=None):
+        if out is None:
+            out = np.empty((self.ny, self.nx), np.float32)
+        p, keep = _ptr(out, np.float32, self.ny * self.nx, writable=True)
+        _check(load().wf_get_field(self.h, int(field), p), "wf_get_field")
+        return out
+
+    def solve(self, d, pixel_var, mask, Cs, P1f, Pst, stripe_amp2, schedule, tol, out=None):
+        if out is None:
+            out = np.empty((self.ny, self.nx), np.float32)
+        ptrs = self._problem_ptrs(d, pixel_var, mask, Cs, P1f, Pst, stripe_amp2)
+        po, keep = _ptr(out, np.float32, self.ny * self.nx, writable=True)
+        st = wf_stats()
+        rc = load().wf_solve(self.h, *ptrs, C.byref(schedule), float(tol), po, C.byref(st))
+        if rc not in (WF_OK, WF_ENOCONV):
+            _check(rc, "wf_solve")
+        return out, st.as_dict()
+
+    def fft2(self, x, inverse=False, rows_only=False, out=None):
+        n = self.ny * self.nx
+        if out is None:
+            out = np.empty(n, np.float32)
+        pi, ki = _ptr(x, np.float32, n)
+        po, ko = _ptr(out, np.float32, n, writable=True)
+        _check(load().wf_fft2(self.h, pi, po, int(bool(inverse)), int(bool(rows_only))), "wf_fft2")
+        return out
+
+
+    def launch_count(self) -> int:
+        return int(load().wf_launch_count(self.h))
+
+    def time_passes(self, lam: float, n: int):
+        """Mean CUDA-event time (us) of the row pass and of the column pass."""
+        r, c = C.c_double(), C.c_double()
+        _check(load().wf_time_passes(self.h, float(lam), int(n), C.byref(r), C.byref(c)), "wf_time_passes")
+        return r.value, c.value
+
+
+def parts_of(prob) -> int:
+    """Parts bit mask for a synth.Problem."""
+    p = WF_PART_WHITE
+    if prob.P1f is not None:
+        p |= WF_PART_1F
+    if prob.Pst is not None:
+        p |= WF_PART_STRIPE
+    return p

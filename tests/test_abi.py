@@ -1,0 +1,92 @@
+"""CPU checks of the boundary: libwf.so builds for sm_103a, loads, and exports
+every function include/wf.h declares; host-side argument checks answer
+without touching a GPU; the product path never reaches the oracle."""
+
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "wf.h")).read()
+    return re.findall(r"^WF_API\s+[\w\s\*]+?\b(wf_\w+)\s*\(", src, flags=re.M)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1704_00865_gb300 import build, wf
+    build.build()
+    return wf.load()
+
+
+def test_header_declares_the_expected_entry_points():
+    names = _declared()
+    from paper_1704_00865_gb300 import wf
+    assert sorted(names) == sorted(wf.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for n in _declared():
+        assert hasattr(lib, n), n
+    # and nothing else with C linkage beyond the declared ABI
+    import subprocess
+    from paper_1704_00865_gb300 import build
+    out = subprocess.run(["nm", "-D", "--defined-only", build.LIB], capture_output=True, text=True).stdout
+    exported = sorted(l.split()[-1] for l in out.splitlines() if " T " in l and l.split()[-1].startswith("wf_"))
+    assert exported == sorted(_declared())
+
+
+def test_host_only_entry_points(lib):
+    from paper_1704_00865_gb300 import wf
+    assert lib.wf_version() == 1
+    assert wf.strerror(0) == "ok"
+    assert "converge" in wf.strerror(3)
+    p = wf.wf_params_default()
+    assert list(p.theta) == [0.9, 0.9, 1.0]
+    assert p.split_f == 0.5 and p.split_w == 0.0
+    assert p.residual_every == 10 and p.check_every == 8
+    assert p.merge_2df == 1 and p.tol_u_scale == 1.0
+
+
+@pytest.mark.parametrize("ny,nx,parts,code", [
+    (1024, 1000, 7, 7),      # not a power of two
+    (16, 1024, 7, 7),        # below the smallest size
+    (8192, 64, 7, 7),        # above the largest size
+    (64, 64, 6, 1),          # white part missing
+    (64, 64, 15, 1),         # unknown part bit
+])
+def test_plan_create_rejects_bad_arguments_before_any_cuda_call(lib, ny, nx, parts, code):
+    h = C.c_void_p()
+    assert lib.wf_plan_create(C.byref(h), ny, nx, parts, None, None) == code
+    assert h.value is None
+
+
+def test_plan_create_rejects_bad_params(lib):
+    from paper_1704_00865_gb300 import wf
+    for kw in (dict(theta=(0.9, 1.5, 1.0)), dict(split_f=1.0, merge_2df=0), dict(split_f=1.01),
+               dict(residual_every=0), dict(tol_u_scale=0.0)):
+        p = wf.make_params(**kw)
+        h = C.c_void_p()
+        assert lib.wf_plan_create(C.byref(h), 64, 64, 7, C.byref(p), None) == wf.WF_EINVAL
+
+
+def test_product_path_never_imports_the_oracle():
+    pkg = os.path.join(ROOT, "paper_1704_00865_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle", src, flags=re.M), f
+                assert "wf_oracle" not in src, f
+
+
+def test_schedule_struct_layout_matches_header(lib):
+    from paper_1704_00865_gb300 import wf
+    # int, ptr, ptr, int, 4 doubles on LP64
+    assert C.sizeof(wf.wf_schedule) == 4 + 4 + 8 + 8 + 4 + 4 + 32
+    assert C.sizeof(wf.wf_params) == 24 + 16 + 8 + 16 + 16
+    assert C.sizeof(wf.wf_stats) == 8 + 8 * 3 + 24 + 8

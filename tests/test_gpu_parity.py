@@ -1,0 +1,187 @@
+"""CUDA path against the FP64 oracle on identical seeded inputs.
+
+* one sweep per noise configuration: every stored field, element by element;
+* scheduled runs (fixed lambda levels, residual checkpoints) through wf_run;
+* the residual the lambda rule and the stop test use;
+* converged solutions against the closed form, dense Cholesky and the
+  single-messenger configuration of the 64 x 64 white-noise workload;
+* edge cases: invalid inputs, masked data values, host versus device
+  buffers, run-to-run determinism.
+
+Tolerance: the FP32 path against FP64 is held to a relative L2 error of
+1e-4 on s (the bar the method's acceptance sets), tighter where one sweep
+leaves no room for error to build up.
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_util import dev, field, make_plan, oracle_fields, rel
+from paper_1704_00865_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def wf():
+    from paper_1704_00865_gb300 import build, wf
+    build.build()
+    wf.load()
+    return wf
+
+
+CONFIGS = {
+    "white": dict(one_over_f=False, stripes=False),
+    "white+1f": dict(stripes=False),
+    "white+stripes": dict(one_over_f=False),
+    "all": dict(),
+    "all+rows": dict(stripe_rows_vary=True),
+}
+
+
+@pytest.mark.parametrize("merge", [0, 1])
+@pytest.mark.parametrize("name", list(CONFIGS))
+@pytest.mark.parametrize("shape", [(64, 128), (128, 32)])
+def test_single_sweep_matches_oracle_field_by_field(wf, name, shape, merge):
+    prob = synth.make_problem(*shape, 11, mask_frac=0.05, **CONFIGS[name])
+    plan = make_plan(prob, merge_2df=merge)
+    P = O.build_parts(prob, merge_2df=bool(merge))
+    ch = O.Chain(P)
+    for lam in (50.0, 3.0):
+        plan.iterate(lam, 1)
+        ch.sweep(lam)
+        for fid, ref in oracle_fields(ch).items():
+            got = field(plan, fid)
+            assert rel(got, ref) < 2e-5, (name, lam, fid, rel(got, ref))
+    plan.close()
+
+
+@pytest.mark.parametrize("merge,split_f", [(0, 0.5), (1, 0.5), (1, 1.0)])
+@pytest.mark.parametrize("shape,seed", [((64, 128), 1), ((256, 256), 2), ((32, 512), 3)])
+def test_scheduled_run_matches_oracle(wf, shape, seed, merge, split_f):
+    prob = synth.make_problem(*shape, seed, mask_frac=0.05, stripe_rows_vary=(seed == 3))
+    lam, its = [300.0, 30.0, 3.0, 1.0], [20, 20, 20, 60]
+    plan = make_plan(prob, residual_every=10, max_iters=120, merge_2df=merge, split_f=split_f)
+    st = plan.run(wf.make_schedule("fixed", lam, its), tol=0.0)
+    r = O.messenger_solve(prob, schedule=O.fixed_schedule(lam, its), n_iters=120, residual_every=10,
+                          merge_2df=bool(merge), split_f=split_f)
+    assert st["iters"] == 120 and st["lam_final"] == 1.0
+    assert rel(field(plan, wf.WF_FIELD_S), r["s"]) < 1e-4
+    # the residual the stop test reads, after the same iterations
+    u, m = plan.residual()
+    assert abs(u - r["rel_u"]) < 1e-3 * r["rel_u"]
+    assert abs(m - r["rel_m"]) < 1e-3 * r["rel_m"]
+    plan.close()
+
+
+def test_adaptive_rule_follows_the_oracle(wf):
+    prob = synth.make_problem(64, 64, 5, mask_frac=0.05)
+    sched = dict(mode="adaptive", lam0=5e5, ratio=1e-2, expo=0.7, snap=1.01)
+    plan = make_plan(prob, residual_every=5, max_iters=300)
+    st = plan.run(wf.make_schedule("adaptive", lam0=5e5, ratio=1e-2, expo=0.7, snap=1.01), tol=0.0)
+    r = O.messenger_solve(prob, schedule=sched, n_iters=300, residual_every=5, merge_2df=True)
+    assert st["iters"] == 300
+    assert st["lam_final"] == pytest.approx(r["lam"], rel=1e-12)
+    assert rel(field(plan, wf.WF_FIELD_S), r["s"]) < 1e-4
+    plan.close()
+
+
+def _solve(wf, prob, sched, tol, **params):
+    plan = make_plan(prob, **params)
+    st = plan.run(sched, tol)
+    s = field(plan, wf.WF_FIELD_S)
+    plan.close()
+    return s, st
+
+
+@pytest.mark.parametrize("n", [256, 1024])
+def test_converges_to_closed_form_homogeneous(wf, n):
+    prob = synth.make_problem(n, n, 21, homogeneous=True, mask_frac=0.0)
+    sched = wf.make_schedule("fixed", O.cooling_levels(1e4, 20), [50] * 20)
+    s, st = _solve(wf, prob, sched, 1e-5, residual_every=10, max_iters=400000, tol_u_scale=10.0,
+                   split_f=1.0)
+    assert st["status"] == 0, st
+    assert rel(s, O.closed_form(prob)) < 1e-4
+
+
+@pytest.mark.parametrize("shape,kw", [((32, 64), dict(stripe_rows_vary=True)), ((64, 32), dict()),
+                                      ((32, 32), dict(one_over_f=False)), ((32, 32), dict(stripes=False))])
+def test_converges_to_dense_cholesky(wf, shape, kw):
+    prob = synth.make_problem(*shape, 31, mask_frac=0.06, k_knee=4.0, k_knee_x=4.0, **kw)
+    sched = wf.make_schedule("fixed", O.cooling_levels(1e2, 5), [20] * 5)
+    s, st = _solve(wf, prob, sched, 1e-6, residual_every=10, max_iters=400000)
+    assert st["status"] == 0, st
+    assert rel(s, O.dense_wf(prob)) < 1e-4
+
+
+def test_single_messenger_64x64_white_noise_workload(wf):
+    # 64 x 64, log-normal white noise, no mask; lambda from 1e3 to 1 over 20
+    # levels of 10 iterations, then lambda = 1 to the tolerance; checked
+    # against the dense Cholesky solution of the 4096 x 4096 system.
+    prob = synth.cfg0_problem(0)
+    sched = wf.make_schedule("fixed", O.cooling_levels(1e3, 20), [10] * 20)
+    s, st = _solve(wf, prob, sched, 1e-6, residual_every=10, max_iters=200000)
+    assert st["status"] == 0
+    s_ref = O.dense_wf(prob)
+    assert rel(s, s_ref) < 1e-4
+    r = O.messenger_solve(prob, schedule=O.fixed_schedule(O.cooling_levels(1e3, 20), [10] * 20),
+                          tol=1e-6, residual_every=10)
+    # the stop test is taken in FP64 on each side's own fields: the same
+    # checkpoint, or a neighbouring one if the residual sits at the threshold
+    assert abs(r["iters"] - st["iters"]) <= 10
+    assert O.literal_residual(prob, s) < 1e-5
+
+
+def test_masked_data_is_ignored_and_nan_there_is_fine(wf):
+    prob = synth.make_problem(64, 64, 41, mask_frac=0.08)
+    a = make_plan(prob)
+    a.iterate(10.0, 5)
+    sa = field(a, wf.WF_FIELD_S)
+    q = synth.Problem(**{**prob.__dict__})
+    q.d = prob.d.copy()
+    q.d[prob.mask.astype(bool)] = np.nan
+    b = make_plan(q)
+    b.iterate(10.0, 5)
+    assert np.array_equal(field(b, wf.WF_FIELD_S), sa)
+
+
+def test_host_buffers_and_device_buffers_agree_bitwise(wf):
+    import torch
+    prob = synth.make_problem(128, 128, 43, mask_frac=0.05)
+    sched = wf.make_schedule("fixed", [30.0, 1.0], [20, 20])
+    p1 = wf.Plan(128, 128, wf.parts_of(prob), wf.make_params(max_iters=40))
+    s_host, st1 = p1.solve(prob.d, prob.pixel_var, prob.mask, prob.C, prob.P1f, prob.Pst, None, sched, 0.0)
+    out = torch.empty(128, 128, device="cuda")
+    p1.solve(dev(prob.d), dev(prob.pixel_var), dev(prob.mask), dev(prob.C), dev(prob.P1f), dev(prob.Pst),
+             None, sched, 0.0, out=out)
+    assert np.array_equal(out.cpu().numpy(), s_host)
+    # and a second identical solve repeats bit for bit
+    s2, _ = p1.solve(prob.d, prob.pixel_var, prob.mask, prob.C, prob.P1f, prob.Pst, None, sched, 0.0)
+    assert np.array_equal(s2, s_host)
+
+
+@pytest.mark.parametrize("what,code", [("nan_d", 1), ("zero_var", 2), ("neg_C", 2), ("asym_C", 1),
+                                       ("all_masked", 1), ("missing_P1f", 1)])
+def test_invalid_inputs_are_rejected(wf, what, code):
+    prob = synth.make_problem(64, 64, 47, mask_frac=0.05)
+    d, var, mask, Cs, P1f = prob.d.copy(), prob.pixel_var.copy(), prob.mask.copy(), prob.C.copy(), prob.P1f
+    if what == "nan_d":
+        idx = np.argwhere(mask == 0)[0]
+        d[tuple(idx)] = np.nan
+    elif what == "zero_var":
+        idx = np.argwhere(mask == 0)[3]
+        var[tuple(idx)] = 0.0
+    elif what == "neg_C":
+        Cs[5, 7] = -1.0
+    elif what == "asym_C":
+        Cs[3, 0] *= 1.5
+    elif what == "all_masked":
+        mask[:] = 1
+    elif what == "missing_P1f":
+        P1f = None
+    plan = wf.Plan(64, 64, wf.parts_of(prob))
+    with pytest.raises(wf.WFError) as e:
+        plan.set_problem(d, var, mask, Cs, P1f, prob.Pst, None)
+    assert e.value.code == code
+    plan.close()
