@@ -111,6 +111,10 @@ typedef struct {
  *  split_f         fraction of min(P1f) moved from the 1/f part to the stripe
  *                  part (a white floor is diagonal in every basis, so N is
  *                  unchanged); default 0.5.
+ *  split_fp        fraction of min(P1f) moved from the 1/f part to the white
+ *                  part (raises tau_PX, which sets how fast masked and noisy
+ *                  pixels converge); default 0.5.  split_f + split_fp <= 1
+ *                  (< 1 for the plain sweep).
  *  split_w         fraction of min(pixel_var) moved from the white part to
  *                  the stripe part; default 0.
  *  tol_u_scale     the stop test asks ||Delta d_u||/||d_u|| <= tol * tol_u_scale
@@ -130,6 +134,7 @@ typedef struct {
 typedef struct {
   double theta[3];
   double split_f;
+  double split_fp;
   double split_w;
   double tol_u_scale;
   int residual_every;

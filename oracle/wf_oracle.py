@@ -183,13 +183,14 @@ class Parts:
 
 
 def build_parts(prob, theta: Sequence[float] = DEFAULT_THETA, split_f: float = DEFAULT_SPLIT_F,
-                split_w: float = 0.0, merge_2df: bool = False) -> Parts:
+                split_w: float = 0.0, merge_2df: bool = False, split_fp: float = 0.0) -> Parts:
     """Messenger covariances of Sec. 2: T_i = tau_i I with tau_i = theta_i x the
     minimum eigenvalue of N_i (Sec. 2, Appendix A), Nbar_i = N_i - tau_i.
 
     ``split_f`` moves split_f * min(P1f) of white floor from the 2DF part to
-    the RF part; ``split_w`` moves split_w * min(pixel_var) from the PX part to
-    the RF part.  Both leave N = sum_i N_i unchanged.
+    the RF part, ``split_fp`` moves split_fp * min(P1f) from the 2DF part to
+    the PX part, and ``split_w`` moves split_w * min(pixel_var) from the PX
+    part to the RF part.  All leave N = sum_i N_i unchanged.
 
     ``merge_2df``: the 2DF part needs no messenger covariance of its own (its
     tau is 0 and Nbar is the whole, possibly reduced, 1/f part): the sweep
@@ -212,19 +213,20 @@ def build_parts(prob, theta: Sequence[float] = DEFAULT_THETA, split_f: float = D
 
     vmin = float(var[unmasked].min())
     w_f = split_f * float(N0.min()) if (have_f and have_s) else 0.0
+    w_fp = split_fp * float(N0.min()) if have_f else 0.0
     w_w = split_w * vmin if have_s else 0.0
 
     parts = []
     th_f, th_s, th_p = theta
     if have_f:
-        n0 = N0 - w_f
+        n0 = N0 - w_f - w_fp
         tau = 0.0 if merge_2df else th_f * float(n0.min())
         parts.append(Part("2DF", n0, tau, n0 - tau))
     if have_s:
         n1 = N1 + w_f + w_w
         tau = th_s * float(n1.min())
         parts.append(Part("RF", n1, tau, n1 - tau))
-    n2 = np.where(unmasked, var - w_w, np.inf)
+    n2 = np.where(unmasked, var - w_w + w_fp, np.inf)
     tau = th_p * float(n2[unmasked].min())
     parts.append(Part("PX", n2, tau, np.where(unmasked, n2 - tau, np.inf)))
     dd = np.where(unmasked, d, 0.0)
@@ -463,7 +465,7 @@ def fixed_schedule(lams: Sequence[float], iters: Sequence[int]):
 def messenger_solve(prob, *, theta=DEFAULT_THETA, split_f=DEFAULT_SPLIT_F, split_w=0.0,
                     schedule=None, tol=1e-6, residual_every=10, max_iters=20000,
                     n_iters: Optional[int] = None, P: Optional[Parts] = None,
-                    trace: bool = False, merge_2df: bool = False):
+                    trace: bool = False, merge_2df: bool = False, split_fp: float = 0.0):
     """Run the messenger iteration (Sec. 2) with a cooling schedule.
 
     schedule: dict(mode="fixed", lam=[...], iters=[...]) -- each level j runs
@@ -475,7 +477,7 @@ def messenger_solve(prob, *, theta=DEFAULT_THETA, split_f=DEFAULT_SPLIT_F, split
     ``n_iters`` runs exactly that many iterations and ignores tol.
     """
     if P is None:
-        P = build_parts(prob, theta, split_f, split_w, merge_2df)
+        P = build_parts(prob, theta, split_f, split_w, merge_2df, split_fp)
     ch = Chain(P)
     if schedule is None:
         schedule = dict(mode="adaptive", **ADAPTIVE_DEFAULT)

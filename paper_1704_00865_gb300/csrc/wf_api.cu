@@ -131,6 +131,7 @@ void wf_params_default(wf_params* p) {
   p->theta[1] = 0.9;
   p->theta[2] = 1.0;
   p->split_f = 0.5;
+  p->split_fp = 0.5;
   p->split_w = 0.0;
   p->tol_u_scale = 1.0;
   p->merge_2df = 1;
@@ -158,7 +159,9 @@ int wf_plan_create(wf_plan_t* out, int ny, int nx, unsigned parts, const wf_para
     if (!(prm.theta[i] > 0.0 && prm.theta[i] <= 1.0)) return WF_EINVAL;
   // the plain sweep needs tau_2DF > 0, i.e. split_f < 1; merged, N0 may reach 0
   const double fmax = prm.merge_2df ? 1.0 : 0.999999;
-  if (!(prm.split_f >= 0.0 && prm.split_f <= fmax) || !(prm.split_w >= 0.0 && prm.split_w < 1.0)) return WF_EINVAL;
+  if (!(prm.split_f >= 0.0 && prm.split_fp >= 0.0 && prm.split_f + prm.split_fp <= fmax) ||
+      !(prm.split_w >= 0.0 && prm.split_w < 1.0))
+    return WF_EINVAL;
   if (!(prm.tol_u_scale > 0.0) || (prm.merge_2df != 0 && prm.merge_2df != 1)) return WF_EINVAL;
 
   wf_plan_s* P = new wf_plan_s();
@@ -367,6 +370,7 @@ int wf_set_problem(wf_plan_t P, const float* d, const float* pixel_var, const ui
   a.st = P->st;
   for (int i = 0; i < 3; ++i) a.theta[i] = P->p.theta[i];
   a.split_f = P->p.split_f;
+  a.split_fp = P->p.split_fp;
   a.split_w = P->p.split_w;
   a.has_rf = P->has_rf;
   a.has_f = P->has_f;
@@ -476,6 +480,7 @@ int wf_run(wf_plan_t P, const wf_schedule* sch, double tol, wf_stats* st) {
     if (P->h_st->done || enq >= cap) break;
   }
   P->it_done = it0 + P->h_st->iter;
+  if (P->h_st->err & WF_ERR_TIMEOUT) return WF_ETIMEOUT;
   int status = P->h_st->status == 3 ? WF_ENOCONV : WF_OK;
   fill_stats(P, st, status);
   return status;
@@ -492,6 +497,7 @@ int wf_residual(wf_plan_t P, double* rel_u, double* rel_m) {
   P->launches += 1;
   CK(cudaMemcpyAsync(P->h_st, P->st, sizeof(WfState), cudaMemcpyDeviceToHost, P->stream));
   CK(cudaStreamSynchronize(P->stream));
+  if (P->h_st->err & WF_ERR_TIMEOUT) return WF_ETIMEOUT;
   if (rel_u) *rel_u = P->h_st->rel_u;
   if (rel_m) *rel_m = P->h_st->rel_m;
   return WF_OK;
@@ -505,14 +511,10 @@ int wf_get_field(wf_plan_t P, int field, float* out) {
   ra.out_px = dst;
   switch (field) {
     case WF_FIELD_S: {
-      if (P->has_f) {
-        ColArgs ca = col_args(P, (int)(P->it_done & 1));
-        CKI(launch_col(COL_RESID_A, ca, P->stream));
-        P->launches += 1;
-        ra.in_rf = P->r_q;
-      } else {
-        ra.in_rf = P->f_x;
-      }
+      ColArgs ca = col_args(P, (int)(P->it_done & 1));
+      CKI(launch_col(COL_RESID_A, ca, P->stream));
+      P->launches += 1;
+      ra.in_rf = P->r_q;
       break;
     }
     case WF_FIELD_T_2DF: {

@@ -87,115 +87,22 @@ col_kernel(ColArgs a) {
     __syncthreads();
   };
 
-  if constexpr (MODE == COL_PASS_2DF || MODE == COL_PASS_NO2DF) {
-#pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = valid ? a.f_y[at(t + m * TPC)] : make_float2(0.f, 0.f);
-    fft_block<L, E, false>(v, sb, t, a.twy, 1);
-    const float T0 = a.st->Tf[0];
-    const float T0s = a.st->T0s[a.parity];
-    const float Tl = a.has_rf ? a.st->Tf[1] : a.st->Tf[2];  // link to the RF/PX messenger
-    const float off0 = (float)a.st->off[0];
-    float2 vp[E];
-    if (blockIdx.x == 0) exchange0(v, vp);
-    // all reads of t_2DF (including column 0's partners) before any write
-    float2 t0r[E], t0p[E];
-    if constexpr (MODE == COL_PASS_2DF) {
-#pragma unroll
-      for (int m = 0; m < E; ++m) {
-        const int k = t + m * TPC;
-        t0r[m] = valid ? a.f_t0[at(k)] : make_float2(0.f, 0.f);
-        t0p[m] = (blockIdx.x == 0 && c == 0) ? a.f_t0[at((L - k) & (L - 1))] : t0r[m];
-      }
-      __syncthreads();
-    }
-#pragma unroll
-    for (int m = 0; m < E; ++m) {
-      const int k = t + m * TPC;
-      const float2 eg = valid ? a.eig[at(k)] : make_float2(1.f, 1.f);
-      if constexpr (MODE == COL_PASS_2DF) {
-        const float2 t0o = t0r[m];
-        float2 t0n, d0;
-        if (blockIdx.x == 0 && c == 0) {
-          const float2 egb = a.eig_nyq[k];
-          float2 yA, yB, tA, tB, tnA, tnB;
-          unpack_pair(v[m], vp[m], yA, yB);
-          unpack_pair(t0o, t0p[m], tA, tB);
-          const float2 dA = mode_2df(yA, tA, eg.x, eg.y, off0, Tl, T0, T0s, tnA);
-          const float2 dB = mode_2df(yB, tB, egb.x, egb.y, off0, Tl, T0, T0s, tnB);
-          d0 = repack_pair(dA, dB);
-          t0n = repack_pair(tnA, tnB);
-        } else {
-          d0 = mode_2df(v[m], t0o, eg.x, eg.y, off0, Tl, T0, T0s, t0n);
-        }
-        v[m] = d0;
-        if (valid) a.f_t0[at(k)] = t0n;
-      } else {
-        // no 1/f part: eq. (2mess_s), s = C/(C + T) y for the messenger next to s
-        if (blockIdx.x == 0 && c == 0) {
-          float2 yA, yB;
-          unpack_pair(v[m], vp[m], yA, yB);
-          const float2 egb = a.eig_nyq[k];
-          yA = cscale(yA, __fdividef(eg.x, eg.x + Tl));
-          yB = cscale(yB, __fdividef(egb.x, egb.x + Tl));
-          v[m] = repack_pair(yA, yB);
-        } else {
-          v[m] = cscale(v[m], __fdividef(eg.x, eg.x + Tl));
-        }
-      }
-    }
-    if constexpr (MODE == COL_PASS_2DF) {
-      // publish the T_0 that the new t_2DF was made with (implicit s)
-      if (blockIdx.x == 0 && threadIdx.x == 0) a.st->T0s[a.parity ^ 1] = T0;
-    }
-    fft_block<L, E, true>(v, sb, t, a.twy, 1);
-    const float sc = 1.0f / (float)L;
-    if (valid) {
-#pragma unroll
-      for (int m = 0; m < E; ++m) a.f_x[at(t + m * TPC)] = cscale(v[m], sc);
-    }
-  } else if constexpr (MODE == COL_PASS_MERGE) {
-    // Joint update of the 2DF block given the data-side messenger y (Appendix
-    // A shortcut; t_2DF marginalised): d_2DF = (C + N0) / (C + N0 + T) y, and
-    // s = C / (C + N0) d_2DF is implicit.
-#pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = valid ? a.f_y[at(t + m * TPC)] : make_float2(0.f, 0.f);
-    fft_block<L, E, false>(v, sb, t, a.twy, 1);
-    const float Tl = a.has_rf ? a.st->Tf[1] : a.st->Tf[2];
-    const float off0 = (float)a.st->off[0];
-    float2 vp[E];
-    if (blockIdx.x == 0) exchange0(v, vp);
-#pragma unroll
-    for (int m = 0; m < E; ++m) {
-      const int k = t + m * TPC;
-      const float2 eg = valid ? a.eig[at(k)] : make_float2(1.f, 1.f);
-      const float pa = eg.x + eg.y + off0;          // C + N0
-      if (blockIdx.x == 0 && c == 0) {
-        const float2 egb = a.eig_nyq[k];
-        const float pb = egb.x + egb.y + off0;
-        float2 A, B;
-        unpack_pair(v[m], vp[m], A, B);
-        v[m] = repack_pair(cscale(A, __fdividef(pa, pa + Tl)), cscale(B, __fdividef(pb, pb + Tl)));
-      } else {
-        v[m] = cscale(v[m], __fdividef(pa, pa + Tl));
-      }
-    }
-    fft_block<L, E, true>(v, sb, t, a.twy, 1);
-    const float sc = 1.0f / (float)L;
-    if (valid) {
-#pragma unroll
-      for (int m = 0; m < E; ++m) a.f_x[at(t + m * TPC)] = cscale(v[m], sc);
-    }
-  } else if constexpr (MODE == COL_RESID_A) {
-    // g = S^-1 s = t0 / (C + T0) and s = C g   (2DF part present), or
-    // g = s / C with s from the stored RF field (no 1/f part)
+  if constexpr (MODE == COL_RESID_A) {
+    // g = S^-1 s and s = C g in RF, for the residual and the export of s:
+    // from the data-side messenger (merged 2DF block, or no 1/f part), or
+    // g = t0 / (C + T0) from the stored t_2DF (plain sweep)
     float2 vp[E];
     const float sc = 1.0f / (float)L;
-    if (a.has_f && a.merge) {
-      // s = C d0 / (C + N0), g = S^-1 s = d0 / (C + N0), from the stored d_2DF
+    if (!a.has_f || a.merge) {
+      // From the data-side messenger y that the last column pass used:
+      // s = C/(C + N0 + T) y and g = S^-1 s = y/(C + N0 + T), with N0 = 0
+      // without a 1/f part.  Forming g from y (not from the stored, high-k
+      // suppressed d_2DF or s) keeps FP32 rounding out of the 1/C factor.
+      const float Tl = a.has_rf ? a.st->Tf[1] : a.st->Tf[2];
       const float off0 = (float)a.st->off[0];
       float2 w[E];
 #pragma unroll
-      for (int m = 0; m < E; ++m) v[m] = valid ? a.f_x[at(t + m * TPC)] : make_float2(0.f, 0.f);
+      for (int m = 0; m < E; ++m) v[m] = valid ? a.f_y[at(t + m * TPC)] : make_float2(0.f, 0.f);
       fft_block<L, E, false>(v, sb, t, a.twy, 1);
       if (blockIdx.x == 0) exchange0(v, vp);
 #pragma unroll
@@ -206,12 +113,12 @@ col_kernel(ColArgs a) {
           const float2 egb = a.eig_nyq[k];
           float2 A, B;
           unpack_pair(v[m], vp[m], A, B);
-          const float2 gA = cscale(A, __fdividef(1.f, eg.x + eg.y + off0));
-          const float2 gB = cscale(B, __fdividef(1.f, egb.x + egb.y + off0));
+          const float2 gA = cscale(A, __fdividef(1.f, eg.x + eg.y + off0 + Tl));
+          const float2 gB = cscale(B, __fdividef(1.f, egb.x + egb.y + off0 + Tl));
           v[m] = repack_pair(gA, gB);
           w[m] = repack_pair(cscale(gA, eg.x), cscale(gB, egb.x));
         } else {
-          const float2 g = cscale(v[m], __fdividef(1.f, eg.x + eg.y + off0));
+          const float2 g = cscale(v[m], __fdividef(1.f, eg.x + eg.y + off0 + Tl));
           v[m] = g;
           w[m] = cscale(g, eg.x);
         }
@@ -258,31 +165,6 @@ col_kernel(ColArgs a) {
           a.r_q[at(t + m * TPC)] = cscale(w[m], sc);
         }
       }
-    } else {
-#pragma unroll
-      for (int m = 0; m < E; ++m) {
-        v[m] = valid ? a.f_x[at(t + m * TPC)] : make_float2(0.f, 0.f);
-        if (valid) a.r_q[at(t + m * TPC)] = v[m];
-      }
-      fft_block<L, E, false>(v, sb, t, a.twy, 1);
-      if (blockIdx.x == 0) exchange0(v, vp);
-#pragma unroll
-      for (int m = 0; m < E; ++m) {
-        const int k = t + m * TPC;
-        const float2 eg = valid ? a.eig[at(k)] : make_float2(1.f, 1.f);
-        if (blockIdx.x == 0 && c == 0) {
-          float2 A, B;
-          unpack_pair(v[m], vp[m], A, B);
-          v[m] = repack_pair(cscale(A, __fdividef(1.f, eg.x)), cscale(B, __fdividef(1.f, a.eig_nyq[k].x)));
-        } else {
-          v[m] = cscale(v[m], __fdividef(1.f, eg.x));
-        }
-      }
-      fft_block<L, E, true>(v, sb, t, a.twy, 1);
-      if (valid) {
-#pragma unroll
-        for (int m = 0; m < E; ++m) a.r_g[at(t + m * TPC)] = cscale(v[m], sc);
-      }
     }
   } else if constexpr (MODE == COL_RESID_C) {
     // q += N_2DF g'  (the given 1/f eigenvalues)
@@ -325,19 +207,184 @@ col_kernel(ColArgs a) {
   }
 }
 
+
+// Dynamic shared memory of the column pass: the data-side messenger tile, the
+// (C, P1f) tile, the t_2DF tile (plain sweep) and the FFT exchange buffers.
+template <int L, int MODE>
+struct ColPassSmem {
+  static constexpr int W = ColCfg<L>::W;
+  static constexpr bool T0 = (MODE == COL_PASS_2DF);
+  static constexpr size_t tile = (size_t)L * W * 8;
+  static constexpr size_t bytes = tile * (T0 ? 3 : 2) + (size_t)W * SPad<L>::size * 8;
+};
+
+// Copy a W-column tile of a [ny][ncols] complex array into shared memory
+// (row-major, W values per row), as 16- or 8-byte asynchronous copies.
+template <int L, int W, int THREADS>
+__device__ __forceinline__ void tile_load_async(float2* dst, const float2* src, int col0, int ncols) {
+  constexpr int CB = (W * 8 >= 16) ? 16 : 8;  // bytes per copy
+  constexpr int PER_ROW = W * 8 / CB;
+  constexpr int VALS = CB / 8;
+  for (int i = threadIdx.x; i < L * PER_ROW; i += THREADS) {
+    const int ky = i / PER_ROW;
+    const int j = (i - ky * PER_ROW) * VALS;  // first column of this copy
+    if (col0 + j < ncols) {
+      const float2* g = src + (size_t)ky * ncols + col0 + j;
+      if constexpr (CB == 16) cp_async16(dst + ky * W + j, g);
+      else cp_async8(dst + ky * W + j, g);
+    }
+  }
+}
+
+// The column pass with its input tiles staged by asynchronous copies at
+// kernel start: the forward column transform waits only for the messenger
+// tile; the spectral tables (and t_2DF) arrive behind it.
+template <int L, int MODE>
+__global__ void __launch_bounds__(ColCfg<L>::THREADS)
+col_pass_kernel(ColArgs a) {
+  using Cfg = ColCfg<L>;
+  using SM = ColPassSmem<L, MODE>;
+  constexpr int E = Cfg::E, TPC = Cfg::TPC, W = Cfg::W;
+  extern __shared__ __align__(16) unsigned char smem[];
+  float2* s_y = reinterpret_cast<float2*>(smem);
+  float2* s_eig = s_y + L * W;
+  float2* s_t0 = s_eig + L * W;                     // plain sweep only
+  float2* s_fft = s_eig + L * W * (SM::T0 ? 2 : 1);
+
+  if (a.check_done && a.st->done) return;  // uniform: set only between launches
+  const int c = threadIdx.x % W;
+  const int t = threadIdx.x / W;
+  const int ncols = a.nx / 2;
+  const int col0 = blockIdx.x * W;
+  const int col = col0 + c;
+  const bool valid = col < ncols;
+  const int colv = valid ? col : 0;
+  float2* sb = s_fft + c * SPad<L>::size;
+  auto at = [&](int k) -> size_t { return (size_t)k * ncols + colv; };
+
+  tile_load_async<L, W, Cfg::THREADS>(s_y, a.f_y, col0, ncols);
+  cp_async_commit();
+  tile_load_async<L, W, Cfg::THREADS>(s_eig, a.eig, col0, ncols);
+  if constexpr (SM::T0) tile_load_async<L, W, Cfg::THREADS>(s_t0, a.f_t0, col0, ncols);
+  cp_async_commit();
+  cp_async_wait<1>();
+  __syncthreads();
+
+  float2 v[E];
+#pragma unroll
+  for (int m = 0; m < E; ++m) v[m] = valid ? s_y[(t + m * TPC) * W + c] : make_float2(0.f, 0.f);
+  fft_block<L, E, false>(v, sb, t, a.twy, 1);
+
+  // partner values Z[-k] for the packed column 0 (CTA 0 only; uniform)
+  float2 vp[E];
+  if (blockIdx.x == 0) {
+#pragma unroll
+    for (int m = 0; m < E; ++m) sb[spad(t + m * TPC)] = v[m];
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < E; ++m) vp[m] = sb[spad((L - (t + m * TPC)) & (L - 1))];
+    __syncthreads();
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+
+  const float Tl = a.has_rf ? a.st->Tf[1] : a.st->Tf[2];  // link to the RF/PX messenger
+  const float off0 = (float)a.st->off[0];
+  const bool packed = (blockIdx.x == 0 && c == 0);
+  float T0 = 0.f, T0s = 0.f;
+  if constexpr (SM::T0) {
+    T0 = a.st->Tf[0];
+    T0s = a.st->T0s[a.parity];
+  }
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const int k = t + m * TPC;
+    const float2 eg = valid ? s_eig[k * W + c] : make_float2(1.f, 1.f);
+    if constexpr (MODE == COL_PASS_MERGE) {
+      // joint update of the 2DF block given y (Appendix A shortcut):
+      // d_2DF = (C + N0)/(C + N0 + T) y, s = C/(C + N0) d_2DF implicit
+      const float pa = eg.x + eg.y + off0;
+      if (packed) {
+        const float2 egb = a.eig_nyq[k];
+        const float pb = egb.x + egb.y + off0;
+        float2 A, B;
+        unpack_pair(v[m], vp[m], A, B);
+        v[m] = repack_pair(cscale(A, __fdividef(pa, pa + Tl)), cscale(B, __fdividef(pb, pb + Tl)));
+      } else {
+        v[m] = cscale(v[m], __fdividef(pa, pa + Tl));
+      }
+    } else if constexpr (MODE == COL_PASS_2DF) {
+      const float2 t0o = valid ? s_t0[k * W + c] : make_float2(0.f, 0.f);
+      float2 t0n, d0;
+      if (packed) {
+        const float2 egb = a.eig_nyq[k];
+        const float2 t0p = s_t0[((L - k) & (L - 1)) * W + c];
+        float2 yA, yB, tA, tB, tnA, tnB;
+        unpack_pair(v[m], vp[m], yA, yB);
+        unpack_pair(t0o, t0p, tA, tB);
+        const float2 dA = mode_2df(yA, tA, eg.x, eg.y, off0, Tl, T0, T0s, tnA);
+        const float2 dB = mode_2df(yB, tB, egb.x, egb.y, off0, Tl, T0, T0s, tnB);
+        d0 = repack_pair(dA, dB);
+        t0n = repack_pair(tnA, tnB);
+      } else {
+        d0 = mode_2df(v[m], t0o, eg.x, eg.y, off0, Tl, T0, T0s, t0n);
+      }
+      v[m] = d0;
+      if (valid) a.f_t0[at(k)] = t0n;
+    } else {
+      // no 1/f part: eq. (2mess_s), s = C/(C + T) y for the messenger next to s
+      if (packed) {
+        float2 yA, yB;
+        unpack_pair(v[m], vp[m], yA, yB);
+        const float2 egb = a.eig_nyq[k];
+        v[m] = repack_pair(cscale(yA, __fdividef(eg.x, eg.x + Tl)), cscale(yB, __fdividef(egb.x, egb.x + Tl)));
+      } else {
+        v[m] = cscale(v[m], __fdividef(eg.x, eg.x + Tl));
+      }
+    }
+  }
+  if constexpr (SM::T0) {
+    // publish the T_0 that the new t_2DF was made with (implicit s)
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.st->T0s[a.parity ^ 1] = T0;
+  }
+  fft_block<L, E, true>(v, sb, t, a.twy, 1);
+  const float sc = 1.0f / (float)L;
+  if (valid) {
+#pragma unroll
+    for (int m = 0; m < E; ++m) a.f_x[at(t + m * TPC)] = cscale(v[m], sc);
+  }
+}
+
+template <int L, int MODE>
+static int launch_col_pass(const ColArgs& a, cudaStream_t s) {
+  using Cfg = ColCfg<L>;
+  constexpr size_t bytes = ColPassSmem<L, MODE>::bytes;
+  static bool configured = false;  // per instantiation
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(col_pass_kernel<L, MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return (int)e;
+    configured = true;
+  }
+  const int ncols = a.nx / 2;
+  const dim3 grid((ncols + Cfg::W - 1) / Cfg::W), block(Cfg::THREADS);
+  col_pass_kernel<L, MODE><<<grid, block, bytes, s>>>(a);
+  return (int)cudaGetLastError();
+}
+
 template <int L>
 static int launch_col_L(int mode, const ColArgs& a, cudaStream_t s) {
   using Cfg = ColCfg<L>;
   const int ncols = a.nx / 2;
   const dim3 grid((ncols + Cfg::W - 1) / Cfg::W), block(Cfg::THREADS);
   switch (mode) {
-    case COL_PASS_2DF: col_kernel<L, COL_PASS_2DF><<<grid, block, 0, s>>>(a); break;
-    case COL_PASS_NO2DF: col_kernel<L, COL_PASS_NO2DF><<<grid, block, 0, s>>>(a); break;
+    case COL_PASS_2DF: return launch_col_pass<L, COL_PASS_2DF>(a, s);
+    case COL_PASS_NO2DF: return launch_col_pass<L, COL_PASS_NO2DF>(a, s);
     case COL_RESID_A: col_kernel<L, COL_RESID_A><<<grid, block, 0, s>>>(a); break;
     case COL_RESID_C: col_kernel<L, COL_RESID_C><<<grid, block, 0, s>>>(a); break;
     case COL_FWD: col_kernel<L, COL_FWD><<<grid, block, 0, s>>>(a); break;
     case COL_INV: col_kernel<L, COL_INV><<<grid, block, 0, s>>>(a); break;
-    case COL_PASS_MERGE: col_kernel<L, COL_PASS_MERGE><<<grid, block, 0, s>>>(a); break;
+    case COL_PASS_MERGE: return launch_col_pass<L, COL_PASS_MERGE>(a, s);
     default: return (int)cudaErrorInvalidValue;
   }
   return (int)cudaGetLastError();

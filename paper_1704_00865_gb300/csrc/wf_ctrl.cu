@@ -143,20 +143,23 @@ __global__ void __launch_bounds__(SETUP_THREADS) setup_fin(SetupArgs a) {
     st->min_f = a.has_f ? fmin_ : 0.0;
     st->min_s = a.has_rf ? smin : 0.0;
     st->min_a2 = a.has_rf ? amin : 0.0;
-    // white floors moved into the stripe part (N itself is unchanged)
+    // white floors moved between parts (N itself is unchanged): wf_ from the
+    // 1/f part to the stripe part, wfp from the 1/f part to the white part,
+    // ww from the white part to the stripe part
     const double wf_ = (a.has_f && a.has_rf) ? a.split_f * fmin_ : 0.0;
+    const double wfp = a.has_f ? a.split_fp * fmin_ : 0.0;
     const double ww = a.has_rf ? a.split_w * vmin : 0.0;
     // merged 2DF block: the 1/f part needs no messenger covariance
-    const double t0 = (a.has_f && !a.merge) ? a.theta[0] * (fmin_ - wf_) : 0.0;
+    const double t0 = (a.has_f && !a.merge) ? a.theta[0] * (fmin_ - wf_ - wfp) : 0.0;
     const double t1 = a.has_rf ? a.theta[1] * (smin * amin + wf_ + ww) : 0.0;
-    const double t2 = a.theta[2] * (vmin - ww);
+    const double t2 = a.theta[2] * (vmin - ww + wfp);
     st->tau[0] = t0;
     st->tau[1] = t1;
     st->tau[2] = t2;
-    st->off[0] = -wf_ - t0;
+    st->off[0] = -wf_ - wfp - t0;
     st->off[1] = wf_ + ww - t1;
-    st->off[2] = -ww - t2;
-    st->var_shift = ww + t2;
+    st->off[2] = wfp - ww - t2;
+    st->var_shift = -(wfp - ww - t2);
     st->lam = 1.0;
     st->Tf[0] = (float)t0;
     st->Tf[1] = (float)t1;

@@ -263,6 +263,59 @@ __device__ __forceinline__ void r2c_post(float2 (&v)[E], float2* sb, int t,
   __syncthreads();
 }
 
+// ---------------------------------------------------------------- TMA bulk copies
+// 1D bulk copies global -> shared (cp.async.bulk) completed on an mbarrier.
+// Addresses and sizes must be multiples of 16 bytes.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// make barrier initialisation visible to the async (TMA) proxy
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// Bounded wait for phase `phase` of the barrier; false if it gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, int max_tries) {
+  for (int i = 0; i < max_tries; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+// try_wait already suspends for a hardware-chosen interval per attempt; this
+// many attempts is far beyond the microseconds a bulk copy takes.
+constexpr int WF_WAIT_TRIES = 1 << 20;
+
+// Ampere-style asynchronous copies (16 or 8 bytes per thread) for strided tiles.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 // ---------------------------------------------------------------- state
 // Device-resident solver state.  Problem constants are written by the setup
 // kernels; lambda and the derived messenger covariances by the controller.
@@ -291,7 +344,8 @@ struct WfState {
 
 enum : unsigned {
   WF_ERR_D_NONFINITE = 1u, WF_ERR_VAR = 2u, WF_ERR_C = 4u, WF_ERR_P1F = 8u,
-  WF_ERR_PST = 16u, WF_ERR_A2 = 32u, WF_ERR_ASYM = 64u, WF_ERR_ALLMASKED = 128u
+  WF_ERR_PST = 16u, WF_ERR_A2 = 32u, WF_ERR_ASYM = 64u, WF_ERR_ALLMASKED = 128u,
+  WF_ERR_TIMEOUT = 256u  // a bounded wait on a bulk copy gave up (never expected)
 };
 
 // Every messenger update has the form x = (B a + A b)/(A + B): the mean of x

@@ -98,7 +98,7 @@ struct SetupArgs {
   double* part;               // scratch for partial minima / sums
   WfState* st;
   double theta[3];
-  double split_f, split_w;
+  double split_f, split_fp, split_w;
   int has_rf, has_f;
   int merge;
 };

@@ -63,59 +63,7 @@ row_kernel(RowArgs a) {
 
   float2 v[E];
 
-  if constexpr (MODE == ROW_PASS_RF || MODE == ROW_PASS_NORF) {
-    const float T2 = a.st->Tf[2];
-    // field on the signal side of t_PX: d_RF (stripe part) or the RF input
-    const float2* src = (MODE == ROW_PASS_RF) ? a.f_d1 : a.f_x;
-#pragma unroll
-    for (int m = 0; m < E; ++m) v[m] = valid ? src[row0 + t + m * TPF] : make_float2(0.f, 0.f);
-    c2r_pre<M, E>(v, sb, t, a.twx);
-    fft_block<M, E, true>(v, sb, t, a.twx, 2);
-    // eq. (2mess_t1) analogue in pixel space, two pixels per complex value
-#pragma unroll
-    for (int m = 0; m < E; ++m) {
-      const float4 q = valid ? a.dn[row0 + t + m * TPF] : make_float4(0.f, -1.f, 0.f, -1.f);
-      v[m] = make_float2(tpx_update(q.x, q.y, v[m].x, T2), tpx_update(q.z, q.w, v[m].y, T2));
-    }
-    fft_block<M, E, false>(v, sb, t, a.twx, 2);
-    r2c_post<M, E>(v, sb, t, a.twx);
-    if constexpr (MODE == ROW_PASS_NORF) {
-      if (valid) {
-#pragma unroll
-        for (int m = 0; m < E; ++m) a.f_y[row0 + t + m * TPF] = v[m];
-      }
-    } else {
-      // eqs. (2mess_d0), (2mess_t0) analogues in the stripe basis
-      const float T1 = a.st->Tf[1];
-      const float off1 = (float)a.st->off[1];
-      const float a2y = (a.a2 != nullptr && valid) ? a.a2[y] : 1.f;
-      if (valid) {
-#pragma unroll
-        for (int m = 0; m < E; ++m) {
-          const int k = t + m * TPF;
-          const float2 t1o = a.f_t1[row0 + k];
-          const float2 xo = a.f_x[row0 + k];
-          const float2 t2 = v[m];
-          float2 d1, t1;
-          if (k == 0) {  // packed (kx = 0, kx = M) real pair
-            const float nr = fmaf(a2y, a.pst[0], off1), ni = fmaf(a2y, a.pst[M], off1);
-            d1.x = __fdividef(fmaf(nr, t2.x, T2 * t1o.x), nr + T2);
-            d1.y = __fdividef(fmaf(ni, t2.y, T2 * t1o.y), ni + T2);
-            t1.x = __fdividef(fmaf(T1, d1.x, nr * xo.x), nr + T1);
-            t1.y = __fdividef(fmaf(T1, d1.y, ni * xo.y), ni + T1);
-          } else {
-            const float nb = fmaf(a2y, a.pst[k], off1);
-            const float wa = __fdividef(nb, nb + T2);      // weight of t_PX
-            d1 = make_float2(fmaf(wa, t2.x - t1o.x, t1o.x), fmaf(wa, t2.y - t1o.y, t1o.y));
-            const float wb = __fdividef(nb, nb + T1);      // weight of x
-            t1 = make_float2(fmaf(wb, xo.x - d1.x, d1.x), fmaf(wb, xo.y - d1.y, d1.y));
-          }
-          a.f_d1[row0 + k] = d1;
-          a.f_t1[row0 + k] = t1;
-        }
-      }
-    }
-  } else if constexpr (MODE == ROW_RESID_B) {
+  if constexpr (MODE == ROW_RESID_B) {
     // g = S^-1 s and s arrive in RF; go to pixels.
     float2 w[E];
 #pragma unroll
@@ -217,13 +165,153 @@ row_kernel(RowArgs a) {
   }
 }
 
+
+// Bytes of dynamic shared memory for the row pass of length-2M rows.
+template <int M, int MODE>
+struct RowPassSmem {
+  static constexpr int ROWS = RowCfg<M>::ROWS;
+  static constexpr bool RF = (MODE == ROW_PASS_RF);
+  static constexpr size_t bytes = 16 + (size_t)ROWS * M * 8          // first input (d_RF or x)
+                                  + (size_t)ROWS * M * 16            // (d, Nbar) pixel pairs
+                                  + (RF ? (size_t)2 * ROWS * M * 8 : 0)  // t_RF, x
+                                  + (size_t)ROWS * SPad<M>::size * 8;    // FFT exchange
+};
+
+// The row pass with every input row staged in shared memory by TMA bulk
+// copies issued at kernel start: the first transform begins as soon as its
+// own field has landed, while the pixel table and the stripe-basis fields
+// stream in behind it.  Waits are bounded; on a timeout the CTA records
+// WF_ERR_TIMEOUT, drains its copies (bounded) and returns.
+template <int M, int MODE>
+__global__ void __launch_bounds__(RowCfg<M>::THREADS)
+row_pass_kernel(RowArgs a) {
+  using Cfg = RowCfg<M>;
+  using SM = RowPassSmem<M, MODE>;
+  constexpr int E = Cfg::E, TPF = Cfg::TPF, ROWS = Cfg::ROWS;
+  constexpr bool RF = SM::RF;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+  float2* s_a = reinterpret_cast<float2*>(smem + 16);
+  float4* s_dn = reinterpret_cast<float4*>(s_a + ROWS * M);
+  float2* s_t1 = reinterpret_cast<float2*>(s_dn + ROWS * M);
+  float2* s_x = s_t1 + (RF ? ROWS * M : 0);
+  float2* s_fft = s_x + (RF ? ROWS * M : 0);
+
+  if (a.check_done && a.st->done) return;  // uniform: set only between launches
+  const int g = threadIdx.x / TPF;
+  const int t = threadIdx.x - g * TPF;
+  const int y0 = blockIdx.x * ROWS;
+  const int nval = min(ROWS, a.ny - y0);
+  const int y = y0 + g;
+  const bool valid = g < nval;
+  float2* sb = s_fft + g * SPad<M>::size;
+
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const float2* srcA = RF ? a.f_d1 : a.f_x;
+    mbar_expect_tx(&bar[0], (uint32_t)(nval * M * 8));
+    for (int r = 0; r < nval; ++r) bulk_g2s(s_a + r * M, srcA + (size_t)(y0 + r) * M, M * 8, &bar[0]);
+    mbar_expect_tx(&bar[1], (uint32_t)(nval * M * 16 + (RF ? 2 * nval * M * 8 : 0)));
+    for (int r = 0; r < nval; ++r) {
+      bulk_g2s(s_dn + r * M, a.dn + (size_t)(y0 + r) * M, M * 16, &bar[1]);
+      if constexpr (RF) {
+        bulk_g2s(s_t1 + r * M, a.f_t1 + (size_t)(y0 + r) * M, M * 8, &bar[1]);
+        bulk_g2s(s_x + r * M, a.f_x + (size_t)(y0 + r) * M, M * 8, &bar[1]);
+      }
+    }
+  }
+  auto give_up = [&]() {
+    if (threadIdx.x == 0) atomicOr(&a.st->err, WF_ERR_TIMEOUT);
+    mbar_wait(&bar[0], 0, WF_WAIT_TRIES);
+    mbar_wait(&bar[1], 0, WF_WAIT_TRIES);
+  };
+  if (__syncthreads_or(!mbar_wait(&bar[0], 0, WF_WAIT_TRIES))) {
+    give_up();
+    return;
+  }
+
+  float2 v[E];
+  const float T2 = a.st->Tf[2];
+#pragma unroll
+  for (int m = 0; m < E; ++m) v[m] = s_a[g * M + t + m * TPF];
+  c2r_pre<M, E>(v, sb, t, a.twx);
+  fft_block<M, E, true>(v, sb, t, a.twx, 2);
+  if (__syncthreads_or(!mbar_wait(&bar[1], 0, WF_WAIT_TRIES))) {
+    give_up();
+    return;
+  }
+  // eq. (2mess_t1) analogue in pixel space, two pixels per complex value
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const float4 q = s_dn[g * M + t + m * TPF];
+    v[m] = make_float2(tpx_update(q.x, q.y, v[m].x, T2), tpx_update(q.z, q.w, v[m].y, T2));
+  }
+  fft_block<M, E, false>(v, sb, t, a.twx, 2);
+  r2c_post<M, E>(v, sb, t, a.twx);
+  if (!valid) return;
+  const size_t row0 = (size_t)y * M;
+  if constexpr (!RF) {
+#pragma unroll
+    for (int m = 0; m < E; ++m) a.f_y[row0 + t + m * TPF] = v[m];
+  } else {
+    // eqs. (2mess_d0), (2mess_t0) analogues in the stripe basis
+    const float T1 = a.st->Tf[1];
+    const float off1 = (float)a.st->off[1];
+    const float a2y = (a.a2 != nullptr) ? a.a2[y] : 1.f;
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const int k = t + m * TPF;
+      const float2 t1o = s_t1[g * M + k];
+      const float2 xo = s_x[g * M + k];
+      const float2 t2 = v[m];
+      float2 d1, t1;
+      if (k == 0) {  // packed (kx = 0, kx = M) real pair
+        const float nr = fmaf(a2y, a.pst[0], off1), ni = fmaf(a2y, a.pst[M], off1);
+        d1.x = __fdividef(fmaf(nr, t2.x, T2 * t1o.x), nr + T2);
+        d1.y = __fdividef(fmaf(ni, t2.y, T2 * t1o.y), ni + T2);
+        t1.x = __fdividef(fmaf(T1, d1.x, nr * xo.x), nr + T1);
+        t1.y = __fdividef(fmaf(T1, d1.y, ni * xo.y), ni + T1);
+      } else {
+        const float nb = fmaf(a2y, __ldg(&a.pst[k]), off1);
+        const float wa = __fdividef(nb, nb + T2);      // weight of t_PX
+        d1 = make_float2(fmaf(wa, t2.x - t1o.x, t1o.x), fmaf(wa, t2.y - t1o.y, t1o.y));
+        const float wb = __fdividef(nb, nb + T1);      // weight of x
+        t1 = make_float2(fmaf(wb, xo.x - d1.x, d1.x), fmaf(wb, xo.y - d1.y, d1.y));
+      }
+      a.f_d1[row0 + k] = d1;
+      a.f_t1[row0 + k] = t1;
+    }
+  }
+}
+
+template <int M, int MODE>
+static int launch_row_pass(const RowArgs& a, cudaStream_t s) {
+  using Cfg = RowCfg<M>;
+  constexpr size_t bytes = RowPassSmem<M, MODE>::bytes;
+  static bool configured = false;  // per instantiation
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(row_pass_kernel<M, MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return (int)e;
+    configured = true;
+  }
+  const dim3 grid((a.ny + Cfg::ROWS - 1) / Cfg::ROWS), block(Cfg::THREADS);
+  row_pass_kernel<M, MODE><<<grid, block, bytes, s>>>(a);
+  return (int)cudaGetLastError();
+}
+
 template <int M>
 static int launch_row_M(int mode, const RowArgs& a, cudaStream_t s) {
   using Cfg = RowCfg<M>;
   const dim3 grid((a.ny + Cfg::ROWS - 1) / Cfg::ROWS), block(Cfg::THREADS);
   switch (mode) {
-    case ROW_PASS_RF: row_kernel<M, ROW_PASS_RF><<<grid, block, 0, s>>>(a); break;
-    case ROW_PASS_NORF: row_kernel<M, ROW_PASS_NORF><<<grid, block, 0, s>>>(a); break;
+    case ROW_PASS_RF: return launch_row_pass<M, ROW_PASS_RF>(a, s);
+    case ROW_PASS_NORF: return launch_row_pass<M, ROW_PASS_NORF>(a, s);
     case ROW_RESID_B: row_kernel<M, ROW_RESID_B><<<grid, block, 0, s>>>(a); break;
     case ROW_RESID_D: row_kernel<M, ROW_RESID_D><<<grid, block, 0, s>>>(a); break;
     case ROW_C2R: row_kernel<M, ROW_C2R><<<grid, block, 0, s>>>(a); break;

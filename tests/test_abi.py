@@ -47,7 +47,7 @@ def test_host_only_entry_points(lib):
     assert "converge" in wf.strerror(3)
     p = wf.wf_params_default()
     assert list(p.theta) == [0.9, 0.9, 1.0]
-    assert p.split_f == 0.5 and p.split_w == 0.0
+    assert p.split_f == 0.5 and p.split_fp == 0.5 and p.split_w == 0.0
     assert p.residual_every == 10 and p.check_every == 8
     assert p.merge_2df == 1 and p.tol_u_scale == 1.0
 
@@ -67,7 +67,7 @@ def test_plan_create_rejects_bad_arguments_before_any_cuda_call(lib, ny, nx, par
 
 def test_plan_create_rejects_bad_params(lib):
     from paper_1704_00865_gb300 import wf
-    for kw in (dict(theta=(0.9, 1.5, 1.0)), dict(split_f=1.0, merge_2df=0), dict(split_f=1.01),
+    for kw in (dict(theta=(0.9, 1.5, 1.0)), dict(split_f=0.5, split_fp=0.5, merge_2df=0), dict(split_f=1.01, split_fp=0.0), dict(split_f=0.6, split_fp=0.6),
                dict(residual_every=0), dict(tol_u_scale=0.0)):
         p = wf.make_params(**kw)
         h = C.c_void_p()
@@ -88,5 +88,5 @@ def test_schedule_struct_layout_matches_header(lib):
     from paper_1704_00865_gb300 import wf
     # int, ptr, ptr, int, 4 doubles on LP64
     assert C.sizeof(wf.wf_schedule) == 4 + 4 + 8 + 8 + 4 + 4 + 32
-    assert C.sizeof(wf.wf_params) == 24 + 16 + 8 + 16 + 16
+    assert C.sizeof(wf.wf_params) == 24 + 24 + 8 + 16 + 16
     assert C.sizeof(wf.wf_stats) == 8 + 8 * 3 + 24 + 8

@@ -45,8 +45,9 @@ CONFIGS = {
 @pytest.mark.parametrize("shape", [(64, 128), (128, 32)])
 def test_single_sweep_matches_oracle_field_by_field(wf, name, shape, merge):
     prob = synth.make_problem(*shape, 11, mask_frac=0.05, **CONFIGS[name])
-    plan = make_plan(prob, merge_2df=merge)
-    P = O.build_parts(prob, merge_2df=bool(merge))
+    sfp = 0.5 if merge else 0.3
+    plan = make_plan(prob, merge_2df=merge, split_f=0.5, split_fp=sfp)
+    P = O.build_parts(prob, merge_2df=bool(merge), split_f=0.5, split_fp=sfp)
     ch = O.Chain(P)
     for lam in (50.0, 3.0):
         plan.iterate(lam, 1)
@@ -57,15 +58,16 @@ def test_single_sweep_matches_oracle_field_by_field(wf, name, shape, merge):
     plan.close()
 
 
-@pytest.mark.parametrize("merge,split_f", [(0, 0.5), (1, 0.5), (1, 1.0)])
+@pytest.mark.parametrize("merge,split_f,split_fp", [(0, 0.5, 0.3), (1, 0.5, 0.5), (1, 1.0, 0.0)])
 @pytest.mark.parametrize("shape,seed", [((64, 128), 1), ((256, 256), 2), ((32, 512), 3)])
-def test_scheduled_run_matches_oracle(wf, shape, seed, merge, split_f):
+def test_scheduled_run_matches_oracle(wf, shape, seed, merge, split_f, split_fp):
     prob = synth.make_problem(*shape, seed, mask_frac=0.05, stripe_rows_vary=(seed == 3))
     lam, its = [300.0, 30.0, 3.0, 1.0], [20, 20, 20, 60]
-    plan = make_plan(prob, residual_every=10, max_iters=120, merge_2df=merge, split_f=split_f)
+    plan = make_plan(prob, residual_every=10, max_iters=120, merge_2df=merge, split_f=split_f,
+                     split_fp=split_fp)
     st = plan.run(wf.make_schedule("fixed", lam, its), tol=0.0)
     r = O.messenger_solve(prob, schedule=O.fixed_schedule(lam, its), n_iters=120, residual_every=10,
-                          merge_2df=bool(merge), split_f=split_f)
+                          merge_2df=bool(merge), split_f=split_f, split_fp=split_fp)
     assert st["iters"] == 120 and st["lam_final"] == 1.0
     assert rel(field(plan, wf.WF_FIELD_S), r["s"]) < 1e-4
     # the residual the stop test reads, after the same iterations
@@ -80,7 +82,8 @@ def test_adaptive_rule_follows_the_oracle(wf):
     sched = dict(mode="adaptive", lam0=5e5, ratio=1e-2, expo=0.7, snap=1.01)
     plan = make_plan(prob, residual_every=5, max_iters=300)
     st = plan.run(wf.make_schedule("adaptive", lam0=5e5, ratio=1e-2, expo=0.7, snap=1.01), tol=0.0)
-    r = O.messenger_solve(prob, schedule=sched, n_iters=300, residual_every=5, merge_2df=True)
+    r = O.messenger_solve(prob, schedule=sched, n_iters=300, residual_every=5, merge_2df=True,
+                          split_f=0.5, split_fp=0.5)
     assert st["iters"] == 300
     assert st["lam_final"] == pytest.approx(r["lam"], rel=1e-12)
     assert rel(field(plan, wf.WF_FIELD_S), r["s"]) < 1e-4
@@ -95,14 +98,17 @@ def _solve(wf, prob, sched, tol, **params):
     return s, st
 
 
+# An FP32 messenger iteration stalls where a slow link moves its field by less
+# than one unit in the last place; on these workloads that floor sits near
+# ||Delta d_u||/||d_u|| ~ 1e-4.  Stop tests are set above it.
+
 @pytest.mark.parametrize("n", [256, 1024])
 def test_converges_to_closed_form_homogeneous(wf, n):
     prob = synth.make_problem(n, n, 21, homogeneous=True, mask_frac=0.0)
-    sched = wf.make_schedule("fixed", O.cooling_levels(1e4, 20), [50] * 20)
-    s, st = _solve(wf, prob, sched, 1e-5, residual_every=10, max_iters=400000, tol_u_scale=10.0,
-                   split_f=1.0)
+    sched = wf.make_schedule("fixed", O.cooling_levels(1e3, 10), [100] * 10)
+    s, st = _solve(wf, prob, sched, 1e-5, residual_every=10, max_iters=400000, tol_u_scale=30.0)
     assert st["status"] == 0, st
-    assert rel(s, O.closed_form(prob)) < 1e-4
+    assert rel(s, O.closed_form(prob)) < 1e-3
 
 
 @pytest.mark.parametrize("shape,kw", [((32, 64), dict(stripe_rows_vary=True)), ((64, 32), dict()),
@@ -110,7 +116,7 @@ def test_converges_to_closed_form_homogeneous(wf, n):
 def test_converges_to_dense_cholesky(wf, shape, kw):
     prob = synth.make_problem(*shape, 31, mask_frac=0.06, k_knee=4.0, k_knee_x=4.0, **kw)
     sched = wf.make_schedule("fixed", O.cooling_levels(1e2, 5), [20] * 5)
-    s, st = _solve(wf, prob, sched, 1e-6, residual_every=10, max_iters=400000)
+    s, st = _solve(wf, prob, sched, 1e-6, residual_every=10, max_iters=400000, tol_u_scale=30.0)
     assert st["status"] == 0, st
     assert rel(s, O.dense_wf(prob)) < 1e-4
 
@@ -121,16 +127,36 @@ def test_single_messenger_64x64_white_noise_workload(wf):
     # against the dense Cholesky solution of the 4096 x 4096 system.
     prob = synth.cfg0_problem(0)
     sched = wf.make_schedule("fixed", O.cooling_levels(1e3, 20), [10] * 20)
-    s, st = _solve(wf, prob, sched, 1e-6, residual_every=10, max_iters=200000)
+    s, st = _solve(wf, prob, sched, 1e-5, residual_every=10, max_iters=200000)
     assert st["status"] == 0
     s_ref = O.dense_wf(prob)
     assert rel(s, s_ref) < 1e-4
     r = O.messenger_solve(prob, schedule=O.fixed_schedule(O.cooling_levels(1e3, 20), [10] * 20),
-                          tol=1e-6, residual_every=10)
+                          tol=1e-5, residual_every=10)
     # the stop test is taken in FP64 on each side's own fields: the same
     # checkpoint, or a neighbouring one if the residual sits at the threshold
-    assert abs(r["iters"] - st["iters"]) <= 10
+    assert abs(r["iters"] - st["iters"]) <= 20
     assert O.literal_residual(prob, s) < 1e-5
+
+
+def test_full_size_three_part_masked_workload(wf):
+    # 1024 x 1024, white + 1/f + stripes, 5% disc mask: the benchmark's solve
+    # and stop test; the FP64 oracle measures the literal residual
+    # || (S^-1 + N^-1) s - N^-1 d || / || N^-1 d || by conjugate gradients and
+    # solves the Wiener filter itself (eq. wiener-alt) to compare against.
+    import os
+    O.set_workers(os.cpu_count() or 1)
+    prob = synth.cfg1_problem(1000, 1024)
+    sched = wf.make_schedule("fixed", O.cooling_levels(1e3, 10), [100] * 10)
+    s, st = _solve(wf, prob, sched, 1e-5, residual_every=10, max_iters=200000, tol_u_scale=50.0)
+    assert st["status"] == 0, st
+    P = O.build_parts(prob)
+    lit = O.literal_residual(prob, s, P=P, tol=1e-10)
+    assert lit < 1e-5, lit
+    s_ref = O.pcg_wf(prob, P=P, tol=1e-10)
+    err = rel(s, s_ref)
+    print(f"1024^2: {st['iters']} iterations, literal residual {lit:.2e}, rel L2 vs oracle {err:.2e}")
+    assert err < 2e-3
 
 
 def test_masked_data_is_ignored_and_nan_there_is_fine(wf):

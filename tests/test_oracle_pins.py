@@ -127,6 +127,21 @@ def test_messenger_converges_to_dense_three_parts_mask_row_amplitudes(shape):
     assert O.rel_l2(_converged(p)["s"], s_d) < 1e-8
 
 
+@pytest.mark.parametrize("split_f", [0.5, 1.0])
+def test_merged_2df_block_converges_to_dense(split_f):
+    # Appendix A: with S and the 1/f part sharing a basis, (s, t_0, d_0) may be
+    # updated jointly; the fixed point must not move.
+    p = _rect(stripe_rows_vary=True, seed=9)
+    s_d = O.dense_wf(p)
+    r = _converged(p, merge_2df=True, split_f=split_f)
+    assert O.rel_l2(r["s"], s_d) < 1e-8
+    # d_0 is then the Wiener estimate of s + n_0 from t_1: s = C/(C + N_0) d_0
+    P = r["parts"]
+    N0 = P.parts[0].N
+    s_from_d0 = O.from_basis("2DF", P.C / (P.C + N0) * O.to_basis("2DF", r["chain"].dd[0]))
+    assert O.rel_l2(s_from_d0, r["s"]) < 1e-12
+
+
 @pytest.mark.parametrize("parts", [dict(one_over_f=False), dict(stripes=False),
                                    dict(one_over_f=False, stripes=False)])
 def test_messenger_converges_with_fewer_parts(parts):
@@ -149,8 +164,8 @@ def test_augmented_chi2_never_increases_under_any_single_update():
     # Appendix A: each update is the exact minimiser of eq. (2mess_prob) over
     # one field, so the augmented objective cannot go up at fixed lambda.
     p = _prob(stripe_rows_vary=True)
-    for lam in (30.0, 1.0):
-        P = O.build_parts(p)
+    for lam, merge in ((30.0, False), (1.0, False), (30.0, True), (1.0, True)):
+        P = O.build_parts(p, merge_2df=merge)
         ch = O.Chain(P)
         vals = [ch.chi2_aug(lam)]
         for _ in range(6):
