@@ -124,6 +124,13 @@ typedef struct {
  *                  t_0 is marginalised and s = (S^-1 + N_0^-1)^-1 N_0^-1 d_0);
  *                  the iteration then needs no tau for the 1/f part and
  *                  split_f may be 1.  0: the plain sweep.  Default 1.
+ *  refine          defect-correction solves wf_solve adds after the first
+ *                  (default 0).  Each computes Delta d_u = [(I + N S^-1) s - d]
+ *                  on unmasked pixels for the accumulated s (Sec. 2), solves
+ *                  the same Wiener filter with Delta d_u as data and subtracts
+ *                  the result: WF(Delta d) = s - s_exact up to the masked-pixel
+ *                  term, so each pass removes the FP32 stagnation error of the
+ *                  previous one.  Only wf_solve refines.
  *  residual_every  R: the residual and the lambda rule run every R
  *                  iterations; default 10.
  *  max_iters       default 200000.
@@ -141,7 +148,8 @@ typedef struct {
   int max_iters;
   int check_every;
   int merge_2df;
-  int reserved[4];
+  int refine;
+  int reserved[3];
 } wf_params;
 
 /* Results of a solve. */
@@ -238,8 +246,12 @@ WF_API int wf_get_field(wf_plan_t plan, int field, float* out);
 
 /*
  * wf_solve -- wf_set_problem + wf_run + wf_get_field(WF_FIELD_S): the whole
- * Wiener filter for one map.  s_out [ny][nx] receives s (also when the
- * return value is WF_ENOCONV).  st may be NULL.
+ * Wiener filter for one map, followed by params.refine defect-correction
+ * solves (see wf_params).  s_out [ny][nx] receives s (also when the return
+ * value is WF_ENOCONV).  st may be NULL; with refinement its iters and
+ * checkpoints sum over all solves and rel_rho_* are those of the refined s.
+ * After a refined solve the plan holds the last correction problem: call
+ * wf_set_problem again before wf_run, wf_residual or wf_get_field.
  */
 WF_API int wf_solve(wf_plan_t plan, const float* d, const float* pixel_var,
              const uint8_t* mask, const float* C, const float* P1f,

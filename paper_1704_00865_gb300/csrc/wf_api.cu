@@ -46,6 +46,10 @@ struct wf_plan_s {
   float *stg_pst = nullptr, *stg_a2 = nullptr, *stg_io = nullptr;
   uint8_t* stg_mask = nullptr;
   WfState* h_st = nullptr;  // pinned
+  // defect correction (refine > 0)
+  float4* dn_orig = nullptr;
+  float *s_acc = nullptr, *s_corr = nullptr;
+  float2* rho = nullptr;
   std::vector<void*> allocs;
 };
 
@@ -135,6 +139,7 @@ void wf_params_default(wf_params* p) {
   p->split_w = 0.0;
   p->tol_u_scale = 1.0;
   p->merge_2df = 1;
+  p->refine = 0;
   p->residual_every = 10;
   p->max_iters = 200000;
   p->check_every = 8;
@@ -163,6 +168,7 @@ int wf_plan_create(wf_plan_t* out, int ny, int nx, unsigned parts, const wf_para
       !(prm.split_w >= 0.0 && prm.split_w < 1.0))
     return WF_EINVAL;
   if (!(prm.tol_u_scale > 0.0) || (prm.merge_2df != 0 && prm.merge_2df != 1)) return WF_EINVAL;
+  if (prm.refine < 0 || prm.refine > 8) return WF_EINVAL;
 
   wf_plan_s* P = new wf_plan_s();
   P->ny = ny;
@@ -208,6 +214,12 @@ int wf_plan_create(wf_plan_t* out, int ny, int nx, unsigned parts, const wf_para
   AL(P->stg_pst, (size_t)P->M + 1);
   AL(P->stg_a2, (size_t)ny);
   AL(P->stg_io, npx + 64);
+  if (prm.refine > 0) {
+    AL(P->dn_orig, npx / 2);
+    AL(P->s_acc, npx);
+    AL(P->s_corr, npx);
+    AL(P->rho, npx / 2);
+  }
 #undef AL
   if (rc != WF_OK) {
     wf_plan_destroy(P);
@@ -318,6 +330,29 @@ static int enqueue_residual(wf_plan_s* P, int parity, int check_done) {
   ra.part0 = P->part + 2 * P->nrow;
   CKI(launch_row(ROW_RESID_D, ra, P->stream));
   P->launches += P->has_f ? 4 : 3;
+  return WF_OK;
+}
+
+// Delta d of a pixel-space s against the original data (table dn_orig):
+// rho map (unmasked pixels) and the partial sums of the residual.
+static int enqueue_resid_map(wf_plan_s* P, const float* s_px, float2* rho_out) {
+  RowArgs ra = row_args(P);
+  ra.check_done = 0;
+  ra.dn = P->dn_orig;
+  ra.in_px = (const float2*)s_px;
+  ra.out_rf = P->r_q;
+  CKI(launch_row(ROW_R2C, ra, P->stream));
+  ColArgs ca = col_args(P, 0);
+  ca.check_done = 0;
+  CKI(launch_col(COL_G_FROM_S, ca, P->stream));
+  ra.part0 = P->part;
+  ra.part1 = P->part + P->nrow;
+  CKI(launch_row(ROW_RESID_B, ra, P->stream));
+  if (P->has_f) CKI(launch_col(COL_RESID_C, ca, P->stream));
+  ra.part0 = P->part + 2 * P->nrow;
+  ra.out_px = rho_out;
+  CKI(launch_row(ROW_RESID_D, ra, P->stream));
+  P->launches += P->has_f ? 5 : 4;
   return WF_OK;
 }
 
@@ -556,10 +591,60 @@ int wf_solve(wf_plan_t P, const float* d, const float* pixel_var, const uint8_t*
   if (!s_out) return WF_EINVAL;
   int rc = wf_set_problem(P, d, pixel_var, mask, C, P1f, Pst, stripe_amp2);
   if (rc) return rc;
-  int status = wf_run(P, sched, tol, st);
+  wf_stats s0{};
+  int status = wf_run(P, sched, tol, &s0);
   if (status != WF_OK && status != WF_ENOCONV) return status;
-  rc = wf_get_field(P, WF_FIELD_S, s_out);
-  if (rc) return rc;
+  if (P->p.refine == 0) {
+    rc = wf_get_field(P, WF_FIELD_S, s_out);
+    if (rc) return rc;
+    if (st) *st = s0;
+    return status;
+  }
+  // defect correction: s <- s - WF(Delta d_u(s)), Delta d against the original d
+  const size_t npx = (size_t)P->ny * P->nx;
+  const double du2 = P->h_st->du2;
+  CK(cudaMemcpyAsync(P->dn_orig, P->dn, npx / 2 * sizeof(float4), cudaMemcpyDeviceToDevice, P->stream));
+  if ((rc = wf_get_field(P, WF_FIELD_S, P->s_acc))) return rc;
+  wf_stats tot = s0;
+  const size_t nhb = (size_t)P->ny * P->M * sizeof(float2);
+  for (int r = 0; r < P->p.refine; ++r) {
+    if ((rc = enqueue_resid_map(P, P->s_acc, P->rho))) return rc;
+    CKI(launch_pack_data(P->dn, P->dn_orig, P->rho, npx / 2, P->part + 3 * P->nrow, P->st, P->stream));
+    P->launches += 2;
+    CK(cudaMemsetAsync(P->f_x, 0, nhb, P->stream));
+    if (P->f_d1) CK(cudaMemsetAsync(P->f_d1, 0, nhb, P->stream));
+    if (P->f_t1) CK(cudaMemsetAsync(P->f_t1, 0, nhb, P->stream));
+    if (P->f_y) CK(cudaMemsetAsync(P->f_y, 0, nhb, P->stream));
+    if (P->f_t0) CK(cudaMemsetAsync(P->f_t0, 0, nhb, P->stream));
+    P->it_done = 0;
+    wf_stats sr{};
+    int sr_status = wf_run(P, sched, tol, &sr);
+    if (sr_status != WF_OK && sr_status != WF_ENOCONV) return sr_status;
+    if (sr_status == WF_ENOCONV) status = WF_ENOCONV;
+    tot.iters += sr.iters;
+    tot.checkpoints += sr.checkpoints;
+    if ((rc = wf_get_field(P, WF_FIELD_S, P->s_corr))) return rc;
+    CKI(launch_sub(P->s_acc, P->s_corr, npx, P->stream));
+    P->launches += 1;
+  }
+  // residual of the refined s against the original problem
+  if ((rc = enqueue_resid_map(P, P->s_acc, P->rho))) return rc;
+  CK(cudaMemcpyAsync(&P->st->du2, &du2, sizeof(double), cudaMemcpyHostToDevice, P->stream));
+  CtrlArgs c = ctrl_args(P);
+  c.count_iters = 0;
+  CKI(launch_ctrl(c, P->stream));
+  P->launches += 1;
+  const bool dev = is_device_ptr(s_out);
+  CK(cudaMemcpyAsync(s_out, P->s_acc, npx * sizeof(float), dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     P->stream));
+  CK(cudaMemcpyAsync(P->h_st, P->st, sizeof(WfState), cudaMemcpyDeviceToHost, P->stream));
+  CK(cudaStreamSynchronize(P->stream));
+  // the plan now holds the last correction problem, not the caller's
+  P->loaded = false;
+  tot.rel_rho_u = P->h_st->rel_u;
+  tot.rel_rho_m = P->h_st->rel_m;
+  tot.status = status;
+  if (st) *st = tot;
   return status;
 }
 

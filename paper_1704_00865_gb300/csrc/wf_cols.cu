@@ -195,6 +195,31 @@ col_kernel(ColArgs a) {
         a.r_q[i] = make_float2(fmaf(v[m].x, sc, q.x), fmaf(v[m].y, sc, q.y));
       }
     }
+  } else if constexpr (MODE == COL_G_FROM_S) {
+    // residual of a given s: r_q holds s in RF (kept); r_g <- S^-1 s in RF
+    float2 vp[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) v[m] = valid ? a.r_q[at(t + m * TPC)] : make_float2(0.f, 0.f);
+    fft_block<L, E, false>(v, sb, t, a.twy, 1);
+    if (blockIdx.x == 0) exchange0(v, vp);
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      const int k = t + m * TPC;
+      const float2 eg = valid ? a.eig[at(k)] : make_float2(1.f, 1.f);
+      if (blockIdx.x == 0 && c == 0) {
+        float2 A, B;
+        unpack_pair(v[m], vp[m], A, B);
+        v[m] = repack_pair(cscale(A, __fdividef(1.f, eg.x)), cscale(B, __fdividef(1.f, a.eig_nyq[k].x)));
+      } else {
+        v[m] = cscale(v[m], __fdividef(1.f, eg.x));
+      }
+    }
+    fft_block<L, E, true>(v, sb, t, a.twy, 1);
+    const float sc = 1.0f / (float)L;
+    if (valid) {
+#pragma unroll
+      for (int m = 0; m < E; ++m) a.r_g[at(t + m * TPC)] = cscale(v[m], sc);
+    }
   } else if constexpr (MODE == COL_FWD || MODE == COL_INV) {
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = valid ? a.in[at(t + m * TPC)] : make_float2(0.f, 0.f);
@@ -385,6 +410,7 @@ static int launch_col_L(int mode, const ColArgs& a, cudaStream_t s) {
     case COL_FWD: col_kernel<L, COL_FWD><<<grid, block, 0, s>>>(a); break;
     case COL_INV: col_kernel<L, COL_INV><<<grid, block, 0, s>>>(a); break;
     case COL_PASS_MERGE: return launch_col_pass<L, COL_PASS_MERGE>(a, s);
+    case COL_G_FROM_S: col_kernel<L, COL_G_FROM_S><<<grid, block, 0, s>>>(a); break;
     default: return (int)cudaErrorInvalidValue;
   }
   return (int)cudaGetLastError();

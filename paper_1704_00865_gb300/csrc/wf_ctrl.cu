@@ -235,6 +235,47 @@ __global__ void set_lambda_kernel(WfState* st, double lam, int reset) {
   }
 }
 
+// data of a defect-correction solve: the pixel table with d replaced by rho
+__global__ void __launch_bounds__(SETUP_THREADS)
+pack_data_kernel(float4* dn_out, const float4* dn_in, const float2* rho, size_t npair, double* part) {
+  __shared__ double red[SETUP_THREADS / 32];
+  double s = 0.0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < npair; i += (size_t)gridDim.x * blockDim.x) {
+    const float4 q = dn_in[i];
+    const float2 r = rho[i];
+    const float d0 = q.y < 0.f ? 0.f : r.x, d1 = q.w < 0.f ? 0.f : r.y;
+    dn_out[i] = make_float4(d0, q.y, d1, q.w);
+    s += (double)d0 * d0 + (double)d1 * d1;
+  }
+  double t = block_add<SETUP_THREADS>(s, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(SETUP_THREADS) pack_data_fin(const double* part, WfState* st) {
+  __shared__ double red[SETUP_THREADS / 32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < SETUP_CTAS; i += blockDim.x) s += part[i];
+  s = block_add<SETUP_THREADS>(s, red);
+  if (threadIdx.x == 0) st->du2 = s;
+}
+
+int launch_pack_data(float4* dn_out, const float4* dn_in, const float2* rho, size_t npair, double* part,
+                     WfState* st, cudaStream_t s) {
+  pack_data_kernel<<<SETUP_CTAS, SETUP_THREADS, 0, s>>>(dn_out, dn_in, rho, npair, part);
+  pack_data_fin<<<1, SETUP_THREADS, 0, s>>>(part, st);
+  return (int)cudaGetLastError();
+}
+
+__global__ void sub_kernel(float* y, const float* x, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] -= x[i];
+}
+
+int launch_sub(float* y, const float* x, size_t n, cudaStream_t s) {
+  sub_kernel<<<SETUP_CTAS, SETUP_THREADS, 0, s>>>(y, x, n);
+  return (int)cudaGetLastError();
+}
+
 int launch_set_lambda(WfState* st, double lam, int reset, cudaStream_t s) {
   set_lambda_kernel<<<1, 32, 0, s>>>(st, lam, reset);
   return (int)cudaGetLastError();

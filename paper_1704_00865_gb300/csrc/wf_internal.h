@@ -29,7 +29,8 @@ enum ColMode : int {
   COL_FWD = 4,        // RF -> 2D Fourier
   COL_INV = 5,        // 2D Fourier -> RF (with 1/ny)
   COL_PASS_MERGE = 6, // joint (s, t_2DF, d_2DF) update given the RF messenger
-  COL_NMODES = 7
+  COL_G_FROM_S = 7,   // residual of a given s: g = S^-1 s from s in RF
+  COL_NMODES = 8
 };
 
 struct RowArgs {
@@ -123,5 +124,10 @@ struct CtrlArgs {
 };
 int launch_ctrl(const CtrlArgs& a, cudaStream_t s);
 int launch_set_lambda(WfState* st, double lam, int reset, cudaStream_t s);
+// refinement helpers: dn_out = (rho, Nbar of dn_in) per pixel and ||rho_u||^2
+// into st->du2; and y -= x
+int launch_pack_data(float4* dn_out, const float4* dn_in, const float2* rho, size_t npair,
+                     double* part, WfState* st, cudaStream_t s);
+int launch_sub(float* y, const float* x, size_t n, cudaStream_t s);
 
 }  // namespace wf

@@ -140,6 +140,9 @@ row_kernel(RowArgs a) {
       if (valid) {
         if (q.y >= 0.f) r2 += (double)v[m].x * (double)v[m].x;
         if (q.w >= 0.f) r2 += (double)v[m].y * (double)v[m].y;
+        // optional map of Delta d on unmasked pixels (defect correction)
+        if (a.out_px != nullptr)
+          a.out_px[row0 + t + m * TPF] = make_float2(q.y >= 0.f ? v[m].x : 0.f, q.w >= 0.f ? v[m].y : 0.f);
       }
     }
     double s0 = block_sum<Cfg::THREADS>(r2, red);

@@ -37,7 +37,8 @@ class wf_schedule(C.Structure):
 class wf_params(C.Structure):
     _fields_ = [("theta", C.c_double * 3), ("split_f", C.c_double), ("split_fp", C.c_double),
                 ("split_w", C.c_double), ("tol_u_scale", C.c_double), ("residual_every", C.c_int), ("max_iters", C.c_int),
-                ("check_every", C.c_int), ("merge_2df", C.c_int), ("reserved", C.c_int * 4)]
+                ("check_every", C.c_int), ("merge_2df", C.c_int), ("refine", C.c_int),
+                ("reserved", C.c_int * 3)]
 
 
 class wf_stats(C.Structure):
@@ -142,8 +143,11 @@ def wf_params_default() -> wf_params:
 
 
 def make_params(theta=None, split_f=None, split_w=None, residual_every=None, max_iters=None,
-                check_every=None, merge_2df=None, tol_u_scale=None, split_fp=None) -> wf_params:
+                check_every=None, merge_2df=None, tol_u_scale=None, split_fp=None,
+                refine=None) -> wf_params:
     p = wf_params_default()
+    if refine is not None:
+        p.refine = int(refine)
     if split_fp is not None:
         p.split_fp = float(split_fp)
     if merge_2df is not None:

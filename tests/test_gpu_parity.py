@@ -111,12 +111,34 @@ def test_converges_to_closed_form_homogeneous(wf, n):
     assert rel(s, O.closed_form(prob)) < 1e-3
 
 
+def _solve_refined(wf, prob, sched, tol, refine, **params):
+    import torch
+    ny, nx = prob.shape
+    plan = wf.Plan(ny, nx, wf.parts_of(prob), wf.make_params(refine=refine, **params))
+    out = torch.empty(ny, nx, device="cuda")
+    _, st = plan.solve(dev(prob.d), dev(prob.pixel_var), dev(prob.mask), dev(prob.C), dev(prob.P1f),
+                       dev(prob.Pst), dev(prob.stripe_amp2), sched, tol, out=out)
+    plan.close()
+    return out.cpu().numpy().astype(np.float64), st
+
+
+@pytest.mark.parametrize("n", [256, 1024])
+def test_defect_correction_reaches_closed_form_to_1e4(wf, n):
+    # one defect-correction solve removes the FP32 stagnation error
+    prob = synth.make_problem(n, n, 21, homogeneous=True, mask_frac=0.0)
+    sched = wf.make_schedule("fixed", O.cooling_levels(1e3, 10), [100] * 10)
+    s, st = _solve_refined(wf, prob, sched, 1e-5, 1, residual_every=10, max_iters=400000,
+                           tol_u_scale=30.0)
+    assert st["status"] == 0, st
+    assert rel(s, O.closed_form(prob)) < 1e-4
+
+
 @pytest.mark.parametrize("shape,kw", [((32, 64), dict(stripe_rows_vary=True)), ((64, 32), dict()),
                                       ((32, 32), dict(one_over_f=False)), ((32, 32), dict(stripes=False))])
 def test_converges_to_dense_cholesky(wf, shape, kw):
     prob = synth.make_problem(*shape, 31, mask_frac=0.06, k_knee=4.0, k_knee_x=4.0, **kw)
     sched = wf.make_schedule("fixed", O.cooling_levels(1e2, 5), [20] * 5)
-    s, st = _solve(wf, prob, sched, 1e-6, residual_every=10, max_iters=400000, tol_u_scale=30.0)
+    s, st = _solve_refined(wf, prob, sched, 1e-5, 1, residual_every=10, max_iters=400000, tol_u_scale=10.0)
     assert st["status"] == 0, st
     assert rel(s, O.dense_wf(prob)) < 1e-4
 
@@ -126,17 +148,20 @@ def test_single_messenger_64x64_white_noise_workload(wf):
     # levels of 10 iterations, then lambda = 1 to the tolerance; checked
     # against the dense Cholesky solution of the 4096 x 4096 system.
     prob = synth.cfg0_problem(0)
-    sched = wf.make_schedule("fixed", O.cooling_levels(1e3, 20), [10] * 20)
-    s, st = _solve(wf, prob, sched, 1e-5, residual_every=10, max_iters=200000)
+    levels = O.cooling_levels(1e3, 20)
+    sched = wf.make_schedule("fixed", levels, [10] * 20)
+    s, st = _solve(wf, prob, sched, 1e-4, residual_every=10, max_iters=200000)
     assert st["status"] == 0
-    s_ref = O.dense_wf(prob)
-    assert rel(s, s_ref) < 1e-4
-    r = O.messenger_solve(prob, schedule=O.fixed_schedule(O.cooling_levels(1e3, 20), [10] * 20),
-                          tol=1e-5, residual_every=10)
+    r = O.messenger_solve(prob, schedule=O.fixed_schedule(levels, [10] * 20), tol=1e-4, residual_every=10)
     # the stop test is taken in FP64 on each side's own fields: the same
     # checkpoint, or a neighbouring one if the residual sits at the threshold
     assert abs(r["iters"] - st["iters"]) <= 20
-    assert O.literal_residual(prob, s) < 1e-5
+    assert rel(s, r["s"]) < 1e-4
+    s_ref = O.dense_wf(prob)
+    s2, st2 = _solve_refined(wf, prob, sched, 1e-5, 1, residual_every=10, max_iters=200000, tol_u_scale=10.0)
+    assert st2["status"] == 0, st2
+    assert rel(s2, s_ref) < 1e-4
+    assert O.literal_residual(prob, s2) < 1e-5
 
 
 def test_full_size_three_part_masked_workload(wf):
@@ -157,6 +182,15 @@ def test_full_size_three_part_masked_workload(wf):
     err = rel(s, s_ref)
     print(f"1024^2: {st['iters']} iterations, literal residual {lit:.2e}, rel L2 vs oracle {err:.2e}")
     assert err < 2e-3
+    # with one defect-correction solve the same workload meets rel L2 <= 1e-4
+    s2, st2 = _solve_refined(wf, prob, sched, 1e-5, 1, residual_every=10, max_iters=200000,
+                             tol_u_scale=50.0)
+    assert st2["status"] == 0, st2
+    lit2 = O.literal_residual(prob, s2, P=P, tol=1e-10)
+    err2 = rel(s2, s_ref)
+    print(f"1024^2 refined: {st2['iters']} iterations, literal residual {lit2:.2e}, rel L2 {err2:.2e}")
+    assert lit2 < 1e-5
+    assert err2 < 1e-4
 
 
 def test_masked_data_is_ignored_and_nan_there_is_fine(wf):
