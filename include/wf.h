@@ -291,6 +291,32 @@ WF_API long long wf_launch_count(wf_plan_t plan);
 WF_API int wf_time_passes(wf_plan_t plan, double lam, int n, double* us_row,
                           double* us_col);
 
+/*
+ * wf_fft2_noalloc -- the forward or inverse 2D transform of wf_fft2 without a
+ * plan and without allocating device memory.  The paper has no counterpart:
+ * this entry point exists for callers that are not allowed to call
+ * cudaMalloc -- a library embedded in a host application whose allocator owns
+ * all device memory, or a pipeline that must not allocate once it is running
+ * (an allocation can block, fail or synchronise the device at a bad moment).
+ *   ny, nx   powers of two in [32, 4096] with ny * nx <= 1048576
+ *            (WF_EUNSUPPORTED otherwise)
+ *   in, out  device arrays owned by the caller, laid out as for wf_fft2
+ *            (host pointers give WF_EINVAL)
+ *   inverse  0: real map -> spectrum; 1: spectrum -> real map (1/(ny nx))
+ *   stream   cudaStream_t to launch on; the call returns after launching and
+ *            the result is ready when that stream reaches it
+ * Working memory (the intermediate row-transformed spectrum, up to 4 MiB, and
+ * 64 KiB of twiddle tables) is one fixed device array inside the library that
+ * every GPU loading the library keeps until the process exits.  The first
+ * call on a device looks that array's address up (cudaGetSymbolAddress, with
+ * the device current); make that first call before any stream capture.  All
+ * calls share the array and nothing in it has to start at zero (each call
+ * rewrites what it reads), but calls that overlap on the GPU -- on different
+ * streams, or from different threads -- race with each other.
+ */
+WF_API int wf_fft2_noalloc(int ny, int nx, const float* in, float* out,
+                           int inverse, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

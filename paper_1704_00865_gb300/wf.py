@@ -25,7 +25,7 @@ WF_FIELD_S, WF_FIELD_T_2DF, WF_FIELD_D_2DF, WF_FIELD_T_RF, WF_FIELD_D_RF = range
 # every symbol include/wf.h declares
 EXPORTS = ["wf_version", "wf_strerror", "wf_params_default", "wf_plan_create", "wf_plan_destroy",
            "wf_set_problem", "wf_run", "wf_iterate", "wf_residual", "wf_get_field", "wf_solve",
-           "wf_fft2", "wf_launch_count", "wf_time_passes"]
+           "wf_fft2", "wf_launch_count", "wf_time_passes", "wf_fft2_noalloc"]
 
 
 class wf_schedule(C.Structure):
@@ -92,6 +92,7 @@ def load(path: Optional[str] = None):
     L.wf_fft2.argtypes = [vp, vp, vp, C.c_int, C.c_int]
     L.wf_launch_count.argtypes = [vp]
     L.wf_time_passes.argtypes = [vp, C.c_double, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    L.wf_fft2_noalloc.argtypes = [C.c_int, C.c_int, vp, vp, C.c_int, vp]
     for n in EXPORTS:
         if n not in ("wf_strerror", "wf_params_default", "wf_plan_destroy", "wf_launch_count"):
             getattr(L, n).restype = C.c_int
@@ -302,6 +303,16 @@ class Plan:
         r, c = C.c_double(), C.c_double()
         _check(load().wf_time_passes(self.h, float(lam), int(n), C.byref(r), C.byref(c)), "wf_time_passes")
         return r.value, c.value
+
+
+def wf_fft2_noalloc(ny: int, nx: int, x, out, inverse: bool = False, stream=None):
+    """The 2D transform without a plan or any device allocation (device
+    tensors in and out; see include/wf.h).  Returns after launching."""
+    pi, ki = _ptr(x, np.float32, ny * nx)
+    po, ko = _ptr(out, np.float32, ny * nx, writable=True)
+    _check(load().wf_fft2_noalloc(int(ny), int(nx), pi, po, int(bool(inverse)),
+                                  stream if stream is not None else _current_stream()), "wf_fft2_noalloc")
+    return out
 
 
 def parts_of(prob) -> int:
