@@ -131,6 +131,10 @@ typedef struct {
  *                  the result: WF(Delta d) = s - s_exact up to the masked-pixel
  *                  term, so each pass removes the FP32 stagnation error of the
  *                  previous one.  Only wf_solve refines.
+ *  refine_tol_scale the correction solves stop at tol * refine_tol_scale
+ *                  (their data is the previous residual, so percent-level
+ *                  accuracy already cuts the error by that factor); default
+ *                  100.
  *  residual_every  R: the residual and the lambda rule run every R
  *                  iterations; default 10.
  *  max_iters       default 200000.
@@ -149,7 +153,8 @@ typedef struct {
   int check_every;
   int merge_2df;
   int refine;
-  int reserved[3];
+  double refine_tol_scale;
+  int reserved[2];
 } wf_params;
 
 /* Results of a solve. */
@@ -283,10 +288,11 @@ WF_API int wf_fft2(wf_plan_t plan, const float* in, float* out, int inverse,
 WF_API long long wf_launch_count(wf_plan_t plan);
 
 /*
- * wf_time_passes -- measurement aid: run n further iterations at fixed
- * lambda (as wf_iterate) with CUDA events recorded on the plan's stream
- * around every row pass and every column pass, and return the mean event
- * time of each pass in microseconds.  Changes the state like wf_iterate.
+ * wf_time_passes -- measurement aid: at fixed lambda, capture n row passes
+ * back to back in a CUDA graph and time its replay with CUDA events, then
+ * the same for n column passes; return the mean time per launch of each
+ * pass in microseconds.  The passes overwrite the state, so the plan must
+ * be loaded again (wf_set_problem) before further iteration.
  */
 WF_API int wf_time_passes(wf_plan_t plan, double lam, int n, double* us_row,
                           double* us_col);

@@ -13,6 +13,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "../../include/wf.h"
@@ -50,6 +51,14 @@ struct wf_plan_s {
   float4* dn_orig = nullptr;
   float *s_acc = nullptr, *s_corr = nullptr;
   float2* rho = nullptr;
+  // CUDA graph of one polling chunk of wf_run (K checkpoints of R sweeps),
+  // captured and replayed on the plan's own stream (the caller's stream may
+  // be the legacy default stream, which cannot be captured)
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraphExec_t chunk_exec = nullptr;
+  std::vector<unsigned char> chunk_key;
+  long long chunk_launches = 0;
   std::vector<void*> allocs;
 };
 
@@ -140,6 +149,7 @@ void wf_params_default(wf_params* p) {
   p->tol_u_scale = 1.0;
   p->merge_2df = 1;
   p->refine = 0;
+  p->refine_tol_scale = 100.0;
   p->residual_every = 10;
   p->max_iters = 200000;
   p->check_every = 8;
@@ -147,6 +157,10 @@ void wf_params_default(wf_params* p) {
 
 void wf_plan_destroy(wf_plan_t P) {
   if (!P) return;
+  if (P->chunk_exec) cudaGraphExecDestroy(P->chunk_exec);
+  if (P->ev_in) cudaEventDestroy(P->ev_in);
+  if (P->ev_out) cudaEventDestroy(P->ev_out);
+  if (P->gstream) cudaStreamDestroy(P->gstream);
   for (void* q : P->allocs) cudaFree(q);
   if (P->h_st) cudaFreeHost(P->h_st);
   delete P;
@@ -168,7 +182,7 @@ int wf_plan_create(wf_plan_t* out, int ny, int nx, unsigned parts, const wf_para
       !(prm.split_w >= 0.0 && prm.split_w < 1.0))
     return WF_EINVAL;
   if (!(prm.tol_u_scale > 0.0) || (prm.merge_2df != 0 && prm.merge_2df != 1)) return WF_EINVAL;
-  if (prm.refine < 0 || prm.refine > 8) return WF_EINVAL;
+  if (prm.refine < 0 || prm.refine > 8 || !(prm.refine_tol_scale >= 1.0)) return WF_EINVAL;
 
   wf_plan_s* P = new wf_plan_s();
   P->ny = ny;
@@ -230,6 +244,13 @@ int wf_plan_create(wf_plan_t* out, int ny, int nx, unsigned parts, const wf_para
     P->h_st = nullptr;
     wf_plan_destroy(P);
     return WF_ENOMEM;
+  }
+  if (cudaStreamCreateWithFlags(&P->gstream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&P->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&P->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    wf_plan_destroy(P);
+    return WF_ECUDA;
   }
   // twiddle tables exp(-2 pi i k / n), computed in double on the host
   std::vector<float2> tx(nx), ty(ny);
@@ -456,8 +477,7 @@ static void fill_stats(wf_plan_s* P, wf_stats* st, int status) {
   st->parts = (int)P->parts;
 }
 
-int wf_run(wf_plan_t P, const wf_schedule* sch, double tol, wf_stats* st) {
-  if (!P || !P->loaded || !sch) return WF_EINVAL;
+static int wf_run_on(wf_plan_t P, const wf_schedule* sch, double tol, wf_stats* st) {
   const int R = P->p.residual_every;
   CtrlArgs c = ctrl_args(P);
   c.tol = tol;
@@ -498,18 +518,67 @@ int wf_run(wf_plan_t P, const wf_schedule* sch, double tol, wf_stats* st) {
   long long enq = it0;
   const int K = P->p.check_every;
   const long long cap = it0 + (long long)c.max_iters;
-  for (;;) {
-    for (int cp = 0; cp < K && enq < cap; ++cp) {
+  const long long per_chunk = (long long)K * R;
+  // one chunk: K checkpoints, each R sweeps then the residual and the controller
+  auto enqueue_chunk = [&](long long start) -> int {
+    long long e = start;
+    for (int cp = 0; cp < K && e < cap; ++cp) {
       for (int i = 0; i < R; ++i) {
-        int rc = enqueue_iteration(P, (int)(enq & 1));
+        int rc = enqueue_iteration(P, (int)(e & 1));
         if (rc) return rc;
-        ++enq;
+        ++e;
       }
-      int rc = enqueue_residual(P, (int)(enq & 1), 1);
+      int rc = enqueue_residual(P, (int)(e & 1), 1);
       if (rc) return rc;
       CKI(launch_ctrl(c, P->stream));
       P->launches += 1;
     }
+    return WF_OK;
+  };
+  // Full chunks start on the same sweep parity when K R is even, so one
+  // captured graph replays them all; it is kept while the controller
+  // arguments and the start parity stay the same.
+  std::vector<unsigned char> key(sizeof(CtrlArgs) + 8);
+  memcpy(key.data(), &c, sizeof(CtrlArgs));
+  const long long par = it0 & 1;
+  memcpy(key.data() + sizeof(CtrlArgs), &par, 8);
+  const bool use_graph = (per_chunk % 2 == 0);
+  bool first = true;
+  for (;;) {
+    const bool full = enq + per_chunk <= cap;
+    if (use_graph && full && !first) {
+      if (!P->chunk_exec || P->chunk_key != key) {
+        if (P->chunk_exec) {
+          cudaGraphExecDestroy(P->chunk_exec);
+          P->chunk_exec = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        const long long l0 = P->launches;
+        CK(cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeThreadLocal));
+        int rc = enqueue_chunk(enq);
+        cudaError_t ce = cudaStreamEndCapture(P->stream, &g);
+        if (rc) {
+          if (g) cudaGraphDestroy(g);
+          return rc;
+        }
+        CK(ce);
+        cudaError_t ie = cudaGraphInstantiate(&P->chunk_exec, g, 0);
+        cudaGraphDestroy(g);
+        CK(ie);
+        P->chunk_launches = P->launches - l0;
+        P->launches = l0;
+        P->chunk_key = key;
+      }
+      CK(cudaGraphLaunch(P->chunk_exec, P->stream));
+      P->launches += P->chunk_launches;
+      enq += per_chunk;
+    } else {
+      const long long e0 = enq;
+      int rc = enqueue_chunk(enq);
+      if (rc) return rc;
+      enq = std::min(cap, e0 + per_chunk);
+    }
+    first = false;
     CK(cudaMemcpyAsync(P->h_st, P->st, sizeof(WfState), cudaMemcpyDeviceToHost, P->stream));
     CK(cudaStreamSynchronize(P->stream));
     if (P->h_st->done || enq >= cap) break;
@@ -519,6 +588,21 @@ int wf_run(wf_plan_t P, const wf_schedule* sch, double tol, wf_stats* st) {
   int status = P->h_st->status == 3 ? WF_ENOCONV : WF_OK;
   fill_stats(P, st, status);
   return status;
+}
+
+// The iteration runs on the plan's own stream, ordered after the caller's
+// stream on entry and before it on exit.
+int wf_run(wf_plan_t P, const wf_schedule* sch, double tol, wf_stats* st) {
+  if (!P || !P->loaded || !sch) return WF_EINVAL;
+  cudaStream_t user = P->stream;
+  CK(cudaEventRecord(P->ev_in, user));
+  CK(cudaStreamWaitEvent(P->gstream, P->ev_in, 0));
+  P->stream = P->gstream;
+  int rc = wf_run_on(P, sch, tol, st);
+  P->stream = user;
+  CK(cudaEventRecord(P->ev_out, P->gstream));
+  CK(cudaStreamWaitEvent(user, P->ev_out, 0));
+  return rc;
 }
 
 int wf_residual(wf_plan_t P, double* rel_u, double* rel_m) {
@@ -563,13 +647,18 @@ int wf_get_field(wf_plan_t P, int field, float* out) {
       break;
     }
     case WF_FIELD_D_2DF:
-      if (!P->has_f) return WF_EINVAL;
-      ra.in_rf = P->f_x;
+    case WF_FIELD_T_RF: {
+      // column-tiled fields: to row-major first
+      if (field == WF_FIELD_D_2DF && !P->has_f) return WF_EINVAL;
+      if (field == WF_FIELD_T_RF && !P->has_rf) return WF_EINVAL;
+      ColArgs ca = col_args(P, 0);
+      ca.in = field == WF_FIELD_D_2DF ? P->f_x : P->f_t1;
+      ca.out = P->r_g;
+      CKI(launch_col(COL_UNTILE, ca, P->stream));
+      P->launches += 1;
+      ra.in_rf = P->r_g;
       break;
-    case WF_FIELD_T_RF:
-      if (!P->has_rf) return WF_EINVAL;
-      ra.in_rf = P->f_t1;
-      break;
+    }
     case WF_FIELD_D_RF:
       if (!P->has_rf) return WF_EINVAL;
       ra.in_rf = P->f_d1;
@@ -618,7 +707,7 @@ int wf_solve(wf_plan_t P, const float* d, const float* pixel_var, const uint8_t*
     if (P->f_t0) CK(cudaMemsetAsync(P->f_t0, 0, nhb, P->stream));
     P->it_done = 0;
     wf_stats sr{};
-    int sr_status = wf_run(P, sched, tol, &sr);
+    int sr_status = wf_run(P, sched, tol * P->p.refine_tol_scale, &sr);
     if (sr_status != WF_OK && sr_status != WF_ENOCONV) return sr_status;
     if (sr_status == WF_ENOCONV) status = WF_ENOCONV;
     tot.iters += sr.iters;
@@ -692,34 +781,53 @@ long long wf_launch_count(wf_plan_t P) { return P ? P->launches : -1; }
 
 int wf_time_passes(wf_plan_t P, double lam, int n, double* us_row, double* us_col) {
   if (!P || !P->loaded || n < 1 || !(lam >= 1.0) || !isfinite(lam)) return WF_EINVAL;
-  CKI(launch_set_lambda(P->st, lam, 1, P->stream));
-  P->launches += 1;
-  std::vector<cudaEvent_t> ev(3 * (size_t)n);
-  for (auto& e : ev) CK(cudaEventCreate(&e));
+  // n launches of one pass captured back to back in a graph on the plan's
+  // stream, timed by events around the replay: the per-launch time without
+  // host launch overhead
+  cudaStream_t user = P->stream;
+  P->stream = P->gstream;
   int rc = WF_OK;
-  for (int i = 0; i < n && rc == WF_OK; ++i) {
-    CK(cudaEventRecord(ev[3 * i], P->stream));
-    rc = enqueue_row_pass(P);
-    if (rc) break;
-    CK(cudaEventRecord(ev[3 * i + 1], P->stream));
-    rc = enqueue_col_pass(P, (int)(P->it_done & 1));
-    if (rc) break;
-    CK(cudaEventRecord(ev[3 * i + 2], P->stream));
-    P->it_done++;
+  double res[2] = {0.0, 0.0};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = WF_ECUDA;
+  if (!rc && launch_set_lambda(P->st, lam, 1, P->stream)) rc = WF_ECUDA;
+  // one un-captured launch of each pass first (kernel attributes)
+  if (!rc) rc = enqueue_row_pass(P);
+  if (!rc) rc = enqueue_col_pass(P, (int)(P->it_done & 1));
+  for (int which = 0; which < 2 && !rc; ++which) {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    if (cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      rc = WF_ECUDA;
+      break;
+    }
+    for (int i = 0; i < n && !rc; ++i)
+      rc = which == 0 ? enqueue_row_pass(P) : enqueue_col_pass(P, (int)(P->it_done & 1));
+    cudaError_t ce = cudaStreamEndCapture(P->stream, &g);
+    if (rc || ce != cudaSuccess || cudaGraphInstantiate(&ge, g, 0) != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      rc = rc ? rc : WF_ECUDA;
+      break;
+    }
+    cudaGraphDestroy(g);
+    float ms = 0.f;
+    if (cudaGraphLaunch(ge, P->stream) != cudaSuccess ||  // warm
+        cudaEventRecord(e0, P->stream) != cudaSuccess || cudaGraphLaunch(ge, P->stream) != cudaSuccess ||
+        cudaEventRecord(e1, P->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+      rc = WF_ECUDA;
+    res[which] = 1000.0 * ms / n;
+    cudaGraphExecDestroy(ge);
   }
-  CK(cudaStreamSynchronize(P->stream));
-  double sr = 0.0, sc = 0.0;
-  for (int i = 0; i < n && rc == WF_OK; ++i) {
-    float a = 0.f, b = 0.f;
-    CK(cudaEventElapsedTime(&a, ev[3 * i], ev[3 * i + 1]));
-    CK(cudaEventElapsedTime(&b, ev[3 * i + 1], ev[3 * i + 2]));
-    sr += a;
-    sc += b;
-  }
-  for (auto& e : ev) cudaEventDestroy(e);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamSynchronize(P->stream);
+  P->stream = user;
+  // the state has moved on by an unknown number of column passes
+  P->loaded = false;
   if (rc) return rc;
-  if (us_row) *us_row = 1000.0 * sr / n;
-  if (us_col) *us_col = 1000.0 * sc / n;
+  if (us_row) *us_row = res[0];
+  if (us_col) *us_col = res[1];
   return WF_OK;
 }
 

@@ -25,6 +25,12 @@ struct ColCfg {
   static constexpr int W0 = 256 / TPC;
   static constexpr int W = W0 < 1 ? 1 : (W0 > 32 ? 32 : W0);
   static constexpr int THREADS = W * TPC;
+  // Stride between the per-column FFT buffers (complex values): a half-warp
+  // covers W columns x 16/W consecutive indices, which are bank-conflict free
+  // when the stride is congruent to 16/W modulo 16 (odd for W = 32).
+  static constexpr int SP = SPad<L>::size;
+  static constexpr int WANT = (W >= 32) ? 1 : (16 / W) % 16;
+  static constexpr int STRIDE = SP + ((WANT - SP % 16) + 16) % 16;
 };
 
 __device__ __forceinline__ void unpack_pair(float2 Z, float2 Zp, float2& A, float2& B) {
@@ -58,7 +64,7 @@ __global__ void __launch_bounds__(ColCfg<L>::THREADS)
 col_kernel(ColArgs a) {
   using Cfg = ColCfg<L>;
   constexpr int E = Cfg::E, TPC = Cfg::TPC, W = Cfg::W;
-  __shared__ float2 sbuf[W][SPad<L>::size];
+  __shared__ float2 sbuf[W][Cfg::STRIDE];
 
   const int c = threadIdx.x % W;
   const int t = threadIdx.x / W;
@@ -70,7 +76,8 @@ col_kernel(ColArgs a) {
 
   if (a.check_done && a.st->done) return;  // uniform: set only between launches
 
-  auto at = [&](int k) -> size_t { return (size_t)k * ncols + colv; };
+  auto at = [&](int k) -> size_t { return (size_t)k * ncols + colv; };       // row-major
+  auto att = [&](int k) -> size_t { return tidx(k, colv, a.ny); };           // column-tiled
   float2 v[E];
 
   // Partner value Z[-k] of column 0 (only meaningful where col == 0).  Every
@@ -102,13 +109,13 @@ col_kernel(ColArgs a) {
       const float off0 = (float)a.st->off[0];
       float2 w[E];
 #pragma unroll
-      for (int m = 0; m < E; ++m) v[m] = valid ? a.f_y[at(t + m * TPC)] : make_float2(0.f, 0.f);
+      for (int m = 0; m < E; ++m) v[m] = valid ? a.f_y[att(t + m * TPC)] : make_float2(0.f, 0.f);
       fft_block<L, E, false>(v, sb, t, a.twy, 1);
       if (blockIdx.x == 0) exchange0(v, vp);
 #pragma unroll
       for (int m = 0; m < E; ++m) {
         const int k = t + m * TPC;
-        const float2 eg = valid ? a.eig[at(k)] : make_float2(1.f, 1.f);
+        const float2 eg = valid ? a.eig[att(k)] : make_float2(1.f, 1.f);
         if (blockIdx.x == 0 && c == 0) {
           const float2 egb = a.eig_nyq[k];
           float2 A, B;
@@ -140,7 +147,7 @@ col_kernel(ColArgs a) {
 #pragma unroll
       for (int m = 0; m < E; ++m) {
         const int k = t + m * TPC;
-        const float2 eg = valid ? a.eig[at(k)] : make_float2(1.f, 1.f);
+        const float2 eg = valid ? a.eig[att(k)] : make_float2(1.f, 1.f);
         if (blockIdx.x == 0 && c == 0) {
           const int kp = (L - k) & (L - 1);
           const float2 egb = a.eig_nyq[k];
@@ -176,7 +183,7 @@ col_kernel(ColArgs a) {
 #pragma unroll
     for (int m = 0; m < E; ++m) {
       const int k = t + m * TPC;
-      const float2 eg = valid ? a.eig[at(k)] : make_float2(0.f, 0.f);
+      const float2 eg = valid ? a.eig[att(k)] : make_float2(0.f, 0.f);
       if (blockIdx.x == 0 && c == 0) {
         float2 A, B;
         unpack_pair(v[m], vp[m], A, B);
@@ -205,7 +212,7 @@ col_kernel(ColArgs a) {
 #pragma unroll
     for (int m = 0; m < E; ++m) {
       const int k = t + m * TPC;
-      const float2 eg = valid ? a.eig[at(k)] : make_float2(1.f, 1.f);
+      const float2 eg = valid ? a.eig[att(k)] : make_float2(1.f, 1.f);
       if (blockIdx.x == 0 && c == 0) {
         float2 A, B;
         unpack_pair(v[m], vp[m], A, B);
@@ -220,6 +227,11 @@ col_kernel(ColArgs a) {
 #pragma unroll
       for (int m = 0; m < E; ++m) a.r_g[at(t + m * TPC)] = cscale(v[m], sc);
     }
+  } else if constexpr (MODE == COL_UNTILE) {
+    if (valid) {
+#pragma unroll
+      for (int m = 0; m < E; ++m) a.out[at(t + m * TPC)] = a.in[att(t + m * TPC)];
+    }
   } else if constexpr (MODE == COL_FWD || MODE == COL_INV) {
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = valid ? a.in[at(t + m * TPC)] : make_float2(0.f, 0.f);
@@ -233,48 +245,84 @@ col_kernel(ColArgs a) {
 }
 
 
-// Dynamic shared memory of the column pass: the data-side messenger tile, the
-// (C, P1f) tile, the t_2DF tile (plain sweep) and the FFT exchange buffers.
+// Column pass geometry: W columns per CTA, TPC = L/E threads per column.
+// W is a whole number of column tiles (TMA bulk loads of contiguous tiles)
+// unless the tiles would not fit in shared memory, then half a tile.
+#ifndef WF_COL_E
+#define WF_COL_E 0  // 0: the default choice below; else values per thread (4, 8, 16)
+#endif
 template <int L, int MODE>
-struct ColPassSmem {
-  static constexpr int W = ColCfg<L>::W;
+struct ColPassCfg {
   static constexpr bool T0 = (MODE == COL_PASS_2DF);
+  static constexpr int E = (WF_COL_E > 0 && WF_COL_E <= L / 2) ? WF_COL_E : ((L >= 512) ? 16 : 8);
+  static constexpr int TPC = L / E;
+  static constexpr int W_MIN = (TPC >= 32) ? 1 : 32 / TPC;  // at least one warp
+  // widest staging that fits in 227 KB of shared memory
+  static constexpr int W_FIT = T0 ? (L >= 4096 ? 1 : (L >= 2048 ? 2 : WF_TW)) : (L >= 4096 ? 2 : WF_TW);
+  static constexpr int W_WANT = (W_MIN > W_FIT) ? ((W_MIN + WF_TW - 1) / WF_TW) * WF_TW : W_FIT;
+  static constexpr int W_CAP = 1024 / TPC;  // at most 1024 threads per CTA
+  static constexpr int W = (W_WANT <= W_CAP) ? W_WANT
+                           : (W_CAP >= WF_TW ? (W_CAP / WF_TW) * WF_TW : (W_CAP >= 2 ? 2 : 1));
+  static constexpr bool TILED = (W % WF_TW == 0);
+  static constexpr int THREADS = W * TPC;
+  static constexpr int SP = SPad<L>::size;
+  static constexpr int WANT = (W >= 32) ? 1 : (16 / W) % 16;
+  static constexpr int STRIDE = SP + ((WANT - SP % 16) + 16) % 16;
   static constexpr size_t tile = (size_t)L * W * 8;
-  static constexpr size_t bytes = tile * (T0 ? 3 : 2) + (size_t)W * SPad<L>::size * 8;
+  static constexpr size_t y_off = 16, eig_off = y_off + tile, t0_off = eig_off + tile;
+  static constexpr size_t fft_off = t0_off + (T0 ? tile : 0);
+  static constexpr size_t bytes = fft_off + (size_t)W * STRIDE * 8;
+  // position of (ky, column c of the CTA) in the staged Y / eig tiles
+  static __device__ __forceinline__ int sidx(int ky, int c) {
+    if constexpr (TILED) return (c / WF_TW) * L * WF_TW + ky * WF_TW + (c % WF_TW);
+    else return ky * W + c;
+  }
 };
 
-// Copy a W-column tile of a [ny][ncols] complex array into shared memory
-// (row-major, W values per row), as 16- or 8-byte asynchronous copies.
-template <int L, int W, int THREADS>
-__device__ __forceinline__ void tile_load_async(float2* dst, const float2* src, int col0, int ncols) {
-  constexpr int CB = (W * 8 >= 16) ? 16 : 8;  // bytes per copy
-  constexpr int PER_ROW = W * 8 / CB;
-  constexpr int VALS = CB / 8;
-  for (int i = threadIdx.x; i < L * PER_ROW; i += THREADS) {
-    const int ky = i / PER_ROW;
-    const int j = (i - ky * PER_ROW) * VALS;  // first column of this copy
-    if (col0 + j < ncols) {
-      const float2* g = src + (size_t)ky * ncols + col0 + j;
-      if constexpr (CB == 16) cp_async16(dst + ky * W + j, g);
-      else cp_async8(dst + ky * W + j, g);
+// Stage W columns of a column-tiled field: one bulk copy of whole tiles, or
+// 16-byte asynchronous copies of half-tile rows.
+template <int L, int MODE>
+__device__ __forceinline__ void stage_tiled(float2* dst, const float2* src, int col0, int ny, uint64_t* bar) {
+  using Cfg = ColPassCfg<L, MODE>;
+  if constexpr (Cfg::TILED) {
+    if (threadIdx.x == 0) bulk_g2s(dst, src + tidx(0, col0, ny), (uint32_t)(L * Cfg::W * 8), bar);
+  } else {
+    for (int ky = threadIdx.x; ky < L; ky += Cfg::THREADS) {
+      if constexpr (Cfg::W == 2) cp_async16(dst + ky * 2, src + tidx(ky, col0, ny));
+      else cp_async8(dst + ky, src + tidx(ky, col0, ny));
     }
   }
 }
 
-// The column pass with its input tiles staged by asynchronous copies at
-// kernel start: the forward column transform waits only for the messenger
-// tile; the spectral tables (and t_2DF) arrive behind it.
+// Row-major source (t_2DF of the plain sweep): W columns by async copies.
+template <int L, int W, int THREADS>
+__device__ __forceinline__ void tile_load_rowmajor(float2* dst, const float2* src, int col0, int ncols) {
+  constexpr int CB = (W * 8 >= 16) ? 16 : 8;
+  constexpr int PER_ROW = W * 8 / CB;
+  constexpr int VALS = CB / 8;
+  for (int i = threadIdx.x; i < L * PER_ROW; i += THREADS) {
+    const int ky = i / PER_ROW;
+    const int j = (i - ky * PER_ROW) * VALS;
+    const float2* g = src + (size_t)ky * ncols + col0 + j;
+    if constexpr (CB == 16) cp_async16(dst + ky * W + j, g);
+    else cp_async8(dst + ky * W + j, g);
+  }
+}
+
+// The column pass (Sec. 2 / Appendix A: the 2D-Fourier updates between the
+// forward and inverse column DFTs).  The messenger tile and the (C, P1f)
+// tile are staged in shared memory before the transform begins.
 template <int L, int MODE>
-__global__ void __launch_bounds__(ColCfg<L>::THREADS)
+__global__ void __launch_bounds__(ColPassCfg<L, MODE>::THREADS)
 col_pass_kernel(ColArgs a) {
-  using Cfg = ColCfg<L>;
-  using SM = ColPassSmem<L, MODE>;
+  using Cfg = ColPassCfg<L, MODE>;
   constexpr int E = Cfg::E, TPC = Cfg::TPC, W = Cfg::W;
   extern __shared__ __align__(16) unsigned char smem[];
-  float2* s_y = reinterpret_cast<float2*>(smem);
-  float2* s_eig = s_y + L * W;
-  float2* s_t0 = s_eig + L * W;                     // plain sweep only
-  float2* s_fft = s_eig + L * W * (SM::T0 ? 2 : 1);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
+  float2* s_y = reinterpret_cast<float2*>(smem + Cfg::y_off);
+  float2* s_eig = reinterpret_cast<float2*>(smem + Cfg::eig_off);
+  float2* s_t0 = reinterpret_cast<float2*>(smem + Cfg::t0_off);  // plain sweep only
+  float2* s_fft = reinterpret_cast<float2*>(smem + Cfg::fft_off);
 
   if (a.check_done && a.st->done) return;  // uniform: set only between launches
   const int c = threadIdx.x % W;
@@ -282,22 +330,34 @@ col_pass_kernel(ColArgs a) {
   const int ncols = a.nx / 2;
   const int col0 = blockIdx.x * W;
   const int col = col0 + c;
-  const bool valid = col < ncols;
-  const int colv = valid ? col : 0;
-  float2* sb = s_fft + c * SPad<L>::size;
-  auto at = [&](int k) -> size_t { return (size_t)k * ncols + colv; };
+  float2* sb = s_fft + c * Cfg::STRIDE;
 
-  tile_load_async<L, W, Cfg::THREADS>(s_y, a.f_y, col0, ncols);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(&bar[0], Cfg::TILED ? (uint32_t)Cfg::tile : 0u);
+    mbar_expect_tx(&bar[1], Cfg::TILED ? (uint32_t)Cfg::tile : 0u);
+  }
+  stage_tiled<L, MODE>(s_y, a.f_y, col0, a.ny, &bar[0]);
   cp_async_commit();
-  tile_load_async<L, W, Cfg::THREADS>(s_eig, a.eig, col0, ncols);
-  if constexpr (SM::T0) tile_load_async<L, W, Cfg::THREADS>(s_t0, a.f_t0, col0, ncols);
+  stage_tiled<L, MODE>(s_eig, a.eig, col0, a.ny, &bar[1]);
+  if constexpr (Cfg::T0) tile_load_rowmajor<L, W, Cfg::THREADS>(s_t0, a.f_t0, col0, ncols);
   cp_async_commit();
   cp_async_wait<1>();
-  __syncthreads();
+  if (__syncthreads_or(!mbar_wait(&bar[0], 0, WF_WAIT_TRIES))) {
+    if (threadIdx.x == 0) atomicOr(&a.st->err, WF_ERR_TIMEOUT);
+    mbar_wait(&bar[1], 0, WF_WAIT_TRIES);
+    cp_async_wait<0>();
+    return;
+  }
 
   float2 v[E];
 #pragma unroll
-  for (int m = 0; m < E; ++m) v[m] = valid ? s_y[(t + m * TPC) * W + c] : make_float2(0.f, 0.f);
+  for (int m = 0; m < E; ++m) v[m] = s_y[Cfg::sidx(t + m * TPC, c)];
   fft_block<L, E, false>(v, sb, t, a.twy, 1);
 
   // partner values Z[-k] for the packed column 0 (CTA 0 only; uniform)
@@ -311,20 +371,23 @@ col_pass_kernel(ColArgs a) {
     __syncthreads();
   }
   cp_async_wait<0>();
-  __syncthreads();
+  if (__syncthreads_or(!mbar_wait(&bar[1], 0, WF_WAIT_TRIES))) {
+    if (threadIdx.x == 0) atomicOr(&a.st->err, WF_ERR_TIMEOUT);
+    return;
+  }
 
   const float Tl = a.has_rf ? a.st->Tf[1] : a.st->Tf[2];  // link to the RF/PX messenger
   const float off0 = (float)a.st->off[0];
   const bool packed = (blockIdx.x == 0 && c == 0);
   float T0 = 0.f, T0s = 0.f;
-  if constexpr (SM::T0) {
+  if constexpr (Cfg::T0) {
     T0 = a.st->Tf[0];
     T0s = a.st->T0s[a.parity];
   }
 #pragma unroll
   for (int m = 0; m < E; ++m) {
     const int k = t + m * TPC;
-    const float2 eg = valid ? s_eig[k * W + c] : make_float2(1.f, 1.f);
+    const float2 eg = s_eig[Cfg::sidx(k, c)];
     if constexpr (MODE == COL_PASS_MERGE) {
       // joint update of the 2DF block given y (Appendix A shortcut):
       // d_2DF = (C + N0)/(C + N0 + T) y, s = C/(C + N0) d_2DF implicit
@@ -339,7 +402,7 @@ col_pass_kernel(ColArgs a) {
         v[m] = cscale(v[m], __fdividef(pa, pa + Tl));
       }
     } else if constexpr (MODE == COL_PASS_2DF) {
-      const float2 t0o = valid ? s_t0[k * W + c] : make_float2(0.f, 0.f);
+      const float2 t0o = s_t0[k * W + c];
       float2 t0n, d0;
       if (packed) {
         const float2 egb = a.eig_nyq[k];
@@ -355,7 +418,7 @@ col_pass_kernel(ColArgs a) {
         d0 = mode_2df(v[m], t0o, eg.x, eg.y, off0, Tl, T0, T0s, t0n);
       }
       v[m] = d0;
-      if (valid) a.f_t0[at(k)] = t0n;
+      a.f_t0[(size_t)k * ncols + col] = t0n;
     } else {
       // no 1/f part: eq. (2mess_s), s = C/(C + T) y for the messenger next to s
       if (packed) {
@@ -368,22 +431,20 @@ col_pass_kernel(ColArgs a) {
       }
     }
   }
-  if constexpr (SM::T0) {
+  if constexpr (Cfg::T0) {
     // publish the T_0 that the new t_2DF was made with (implicit s)
     if (blockIdx.x == 0 && threadIdx.x == 0) a.st->T0s[a.parity ^ 1] = T0;
   }
   fft_block<L, E, true>(v, sb, t, a.twy, 1);
   const float sc = 1.0f / (float)L;
-  if (valid) {
 #pragma unroll
-    for (int m = 0; m < E; ++m) a.f_x[at(t + m * TPC)] = cscale(v[m], sc);
-  }
+  for (int m = 0; m < E; ++m) a.f_x[tidx(t + m * TPC, col, a.ny)] = cscale(v[m], sc);
 }
 
 template <int L, int MODE>
 static int launch_col_pass(const ColArgs& a, cudaStream_t s) {
-  using Cfg = ColCfg<L>;
-  constexpr size_t bytes = ColPassSmem<L, MODE>::bytes;
+  using Cfg = ColPassCfg<L, MODE>;
+  constexpr size_t bytes = Cfg::bytes;
   static bool configured = false;  // per instantiation
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(col_pass_kernel<L, MODE>,
@@ -392,7 +453,8 @@ static int launch_col_pass(const ColArgs& a, cudaStream_t s) {
     configured = true;
   }
   const int ncols = a.nx / 2;
-  const dim3 grid((ncols + Cfg::W - 1) / Cfg::W), block(Cfg::THREADS);
+  if (ncols % Cfg::W != 0) return (int)cudaErrorInvalidValue;
+  const dim3 grid(ncols / Cfg::W), block(Cfg::THREADS);
   col_pass_kernel<L, MODE><<<grid, block, bytes, s>>>(a);
   return (int)cudaGetLastError();
 }
@@ -411,6 +473,7 @@ static int launch_col_L(int mode, const ColArgs& a, cudaStream_t s) {
     case COL_INV: col_kernel<L, COL_INV><<<grid, block, 0, s>>>(a); break;
     case COL_PASS_MERGE: return launch_col_pass<L, COL_PASS_MERGE>(a, s);
     case COL_G_FROM_S: col_kernel<L, COL_G_FROM_S><<<grid, block, 0, s>>>(a); break;
+    case COL_UNTILE: col_kernel<L, COL_UNTILE><<<grid, block, 0, s>>>(a); break;
     default: return (int)cudaErrorInvalidValue;
   }
   return (int)cudaGetLastError();

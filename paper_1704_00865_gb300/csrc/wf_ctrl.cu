@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(SETUP_THREADS) setup_spec(SetupArgs a) {
       if (a.C[j] != C) err |= WF_ERR_ASYM;
       if (a.has_f && a.P1f[j] != P) err |= WF_ERR_ASYM;
     }
-    if (kx < h) a.eig[(size_t)ky * h + kx] = make_float2(C, P);
+    if (kx < h) a.eig[tidx(ky, kx, a.ny)] = make_float2(C, P);  // column-tiled
     else a.eig_nyq[ky] = make_float2(C, P);
   }
   if (err) atomicOr(&a.st->err, err);

@@ -142,13 +142,21 @@ struct StageRadix {
   static constexpr int value = rem >= E ? E : rem;
 };
 
+// Barrier between the exchange steps of a transform: the whole block, or
+// only the warp when one warp owns the transform (WARP = true).
+template <bool WARP>
+__device__ __forceinline__ void fft_sync() {
+  if constexpr (WARP) __syncwarp();
+  else __syncthreads();
+}
+
 // One Stockham autosort stage (radix R, sub-transform length NS) of a
 // length-L complex DFT computed by TPF = L/E threads, E values per thread.
 // Inputs are the "natural" layout (thread t holds x[t + m*TPF], m =
 // b + r*(E/R)); outputs go to shared memory at their autosort positions, or,
 // for the last stage, back to the registers in the natural layout.
 // twtab holds exp(-2 pi i k / (L*twstride)), k < L*twstride.
-template <int L, int E, int NS, bool INV>
+template <int L, int E, int NS, bool INV, bool WARP>
 struct FFTStages {
   static __device__ __forceinline__ void run(float2 (&v)[E], float2* sb, int t,
                                              const float2* __restrict__ twtab, int twstride) {
@@ -187,22 +195,22 @@ struct FFTStages {
       }
     }
     if constexpr (!LAST) {
-      __syncthreads();
+      fft_sync<WARP>();
 #pragma unroll
       for (int m = 0; m < E; ++m) v[m] = sb[spad(t + m * TPF)];
-      __syncthreads();
-      FFTStages<L, E, NS * R, INV>::run(v, sb, t, twtab, twstride);
+      fft_sync<WARP>();
+      FFTStages<L, E, NS * R, INV, WARP>::run(v, sb, t, twtab, twstride);
     }
   }
 };
 
-// Full complex DFT of length L (no scaling).  Every thread of the block must
-// call it (it contains __syncthreads); sb is this transform's own padded
+// Full complex DFT of length L (no scaling).  Every thread of the block (or
+// of the warp, WARP = true) must call it; sb is this transform's own padded
 // shared buffer of SPad<L>::size values.
-template <int L, int E, bool INV>
+template <int L, int E, bool INV, bool WARP = false>
 __device__ __forceinline__ void fft_block(float2 (&v)[E], float2* sb, int t,
                                           const float2* __restrict__ twtab, int twstride) {
-  FFTStages<L, E, 1, INV>::run(v, sb, t, twtab, twstride);
+  FFTStages<L, E, 1, INV, WARP>::run(v, sb, t, twtab, twstride);
 }
 
 // ---------------------------------------------------------------- real rows
@@ -213,14 +221,14 @@ __device__ __forceinline__ void fft_block(float2 (&v)[E], float2* sb, int t,
 // Before an inverse complex FFT: X (natural layout in v) -> Z so that
 // IFFT_M(Z) / M gives z.  Here the 1/N scaling of the inverse real DFT is
 // folded in.  twx = exp(-2 pi i k / N).
-template <int M, int E>
+template <int M, int E, bool WARP = false>
 __device__ __forceinline__ void c2r_pre(float2 (&v)[E], float2* sb, int t,
                                         const float2* __restrict__ twx) {
   constexpr int TPF = M / E;
   const float s = 0.5f / (float)M;  // 1/(2M) = 1/N, times the 1/2 of E and O
 #pragma unroll
   for (int m = 0; m < E; ++m) sb[spad(t + m * TPF)] = v[m];
-  __syncthreads();
+  fft_sync<WARP>();
 #pragma unroll
   for (int m = 0; m < E; ++m) {
     const int k = t + m * TPF;
@@ -235,17 +243,17 @@ __device__ __forceinline__ void c2r_pre(float2 (&v)[E], float2* sb, int t,
       v[m] = make_float2((Ek.x - Ok.y) * s, (Ek.y + Ok.x) * s);
     }
   }
-  __syncthreads();
+  fft_sync<WARP>();
 }
 
 // After a forward complex FFT: Z (natural layout) -> packed X.
-template <int M, int E>
+template <int M, int E, bool WARP = false>
 __device__ __forceinline__ void r2c_post(float2 (&v)[E], float2* sb, int t,
                                          const float2* __restrict__ twx) {
   constexpr int TPF = M / E;
 #pragma unroll
   for (int m = 0; m < E; ++m) sb[spad(t + m * TPF)] = v[m];
-  __syncthreads();
+  fft_sync<WARP>();
 #pragma unroll
   for (int m = 0; m < E; ++m) {
     const int k = t + m * TPF;
@@ -260,7 +268,7 @@ __device__ __forceinline__ void r2c_post(float2 (&v)[E], float2* sb, int t,
       v[m] = cadd(Ek, cmul(__ldg(&twx[k]), Ok));
     }
   }
-  __syncthreads();
+  fft_sync<WARP>();
 }
 
 // ---------------------------------------------------------------- TMA bulk copies

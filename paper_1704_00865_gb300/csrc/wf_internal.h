@@ -9,6 +9,18 @@ namespace wf {
 
 struct WfState;
 
+// Fields that both passes touch -- the data-side messenger in RF (t_RF, or
+// t_PX without stripes), the field next to it on the signal side (d_2DF, or
+// s without a 1/f part), and the (C, P1f) table -- are stored in column
+// tiles of WF_TW complex columns: element (y, kx) lives at
+//   (kx / WF_TW) * ny * WF_TW + y * WF_TW + kx % WF_TW,
+// so a column pass reads whole tiles contiguously and a row pass reads
+// 32-byte pieces.  Row-only fields (d_RF, the pixel table) stay row-major.
+constexpr int WF_TW = 4;
+__host__ __device__ __forceinline__ size_t tidx(int y, int kx, int ny) {
+  return (size_t)(kx / WF_TW) * ny * WF_TW + (size_t)y * WF_TW + (kx % WF_TW);
+}
+
 // Row-pass modes (one CTA handles ROWS map rows; each row is one real DFT).
 enum RowMode : int {
   ROW_PASS_RF = 0,    // t_PX update between the row transforms, then d_RF, t_RF
@@ -30,7 +42,8 @@ enum ColMode : int {
   COL_INV = 5,        // 2D Fourier -> RF (with 1/ny)
   COL_PASS_MERGE = 6, // joint (s, t_2DF, d_2DF) update given the RF messenger
   COL_G_FROM_S = 7,   // residual of a given s: g = S^-1 s from s in RF
-  COL_NMODES = 8
+  COL_UNTILE = 8,     // column-tiled RF field -> row-major (exports)
+  COL_NMODES = 9
 };
 
 struct RowArgs {

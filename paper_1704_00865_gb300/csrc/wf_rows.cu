@@ -169,36 +169,71 @@ row_kernel(RowArgs a) {
 }
 
 
-// Bytes of dynamic shared memory for the row pass of length-2M rows.
-template <int M, int MODE>
-struct RowPassSmem {
-  static constexpr int ROWS = RowCfg<M>::ROWS;
-  static constexpr bool RF = (MODE == ROW_PASS_RF);
-  static constexpr size_t bytes = 16 + (size_t)ROWS * M * 8          // first input (d_RF or x)
-                                  + (size_t)ROWS * M * 16            // (d, Nbar) pixel pairs
-                                  + (RF ? (size_t)2 * ROWS * M * 8 : 0)  // t_RF, x
-                                  + (size_t)ROWS * SPad<M>::size * 8;    // FFT exchange
+// Row pass geometry: each row is one real length-2M transform done by TPF
+// threads with E values each -- a single warp per row up to M = 512, so the
+// exchange steps need only warp barriers.  Short rows are packed several to
+// a warp.  One CTA = ROWS rows; the grid is ny / ROWS CTAs, small enough
+// units that the SMs finish within one row of each other.
+#ifndef WF_ROW_E
+#define WF_ROW_E 0  // 0: the default choice below; else values per thread (4, 8, 16)
+#endif
+template <int M>
+struct RowPassCfg {
+  // 8 values per thread (two warps per 1024-point row) measured fastest at
+  // 1024^2; the longest rows take 16 to stay within 1024 threads
+  static constexpr int E_DEF = (M >= 2048) ? 16 : 8;
+  static constexpr int E = (WF_ROW_E > 0 && WF_ROW_E <= M / 2) ? WF_ROW_E : E_DEF;
+  static constexpr int TPF = M / E;
+  static constexpr int ROWS = (TPF >= 32) ? 1 : 32 / TPF;
+  static constexpr int THREADS = ROWS * TPF;
+  static constexpr bool WARP = (THREADS == 32);
 };
 
-// The row pass with every input row staged in shared memory by TMA bulk
-// copies issued at kernel start: the first transform begins as soon as its
-// own field has landed, while the pixel table and the stripe-basis fields
-// stream in behind it.  Waits are bounded; on a timeout the CTA records
-// WF_ERR_TIMEOUT, drains its copies (bounded) and returns.
 template <int M, int MODE>
-__global__ void __launch_bounds__(RowCfg<M>::THREADS)
+struct RowPassSmem {
+  static constexpr int ROWS = RowPassCfg<M>::ROWS;
+  static constexpr bool RF = (MODE == ROW_PASS_RF);
+  static constexpr size_t a_off = 16;
+  static constexpr size_t dn_off = a_off + (size_t)ROWS * M * 8;
+  static constexpr size_t t1_off = dn_off + (size_t)ROWS * M * 16;
+  static constexpr size_t x_off = t1_off + (RF ? (size_t)ROWS * M * 8 : 0);
+  static constexpr size_t fft_off = x_off + (RF ? (size_t)ROWS * M * 8 : 0);
+  static constexpr size_t bytes = fft_off + (size_t)ROWS * SPad<M>::size * 8;
+};
+
+// Gather rows y0 .. y0+nrows-1 of a column-tiled RF field into row-major
+// shared memory, 16 bytes (two complex values) per asynchronous copy.
+template <int M, int THREADS>
+__device__ __forceinline__ void gather_tiled_rows(float2* dst, const float2* src, int y0, int nrows, int ny) {
+  for (int i = threadIdx.x; i < nrows * (M / 2); i += THREADS) {
+    const int r = i / (M / 2);
+    const int k = (i - r * (M / 2)) * 2;
+    cp_async16(dst + r * M + k, src + tidx(y0 + r, k, ny));
+  }
+}
+
+// The row pass (Sec. 2: eq. 2mess_t1 analogue in pixels between the inverse
+// and forward row DFTs, then the stripe-basis updates).  Row-major inputs
+// (d_RF, the pixel table) arrive by TMA bulk copies on an mbarrier, the
+// column-tiled ones (t_RF, the signal-side field) by 16-byte asynchronous
+// copies; the first transform starts as soon as its own field is in.  Waits
+// are bounded; on a timeout the CTA records WF_ERR_TIMEOUT, drains its
+// copies (bounded) and returns.
+template <int M, int MODE>
+__global__ void __launch_bounds__(RowPassCfg<M>::THREADS)
 row_pass_kernel(RowArgs a) {
-  using Cfg = RowCfg<M>;
+  using Cfg = RowPassCfg<M>;
   using SM = RowPassSmem<M, MODE>;
-  constexpr int E = Cfg::E, TPF = Cfg::TPF, ROWS = Cfg::ROWS;
+  constexpr int E = Cfg::E, TPF = Cfg::TPF, ROWS = Cfg::ROWS, NT = Cfg::THREADS;
+  constexpr bool W = Cfg::WARP;
   constexpr bool RF = SM::RF;
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
-  float2* s_a = reinterpret_cast<float2*>(smem + 16);
-  float4* s_dn = reinterpret_cast<float4*>(s_a + ROWS * M);
-  float2* s_t1 = reinterpret_cast<float2*>(s_dn + ROWS * M);
-  float2* s_x = s_t1 + (RF ? ROWS * M : 0);
-  float2* s_fft = s_x + (RF ? ROWS * M : 0);
+  float2* s_a = reinterpret_cast<float2*>(smem + SM::a_off);
+  float4* s_dn = reinterpret_cast<float4*>(smem + SM::dn_off);
+  float2* s_t1 = reinterpret_cast<float2*>(smem + SM::t1_off);
+  float2* s_x = reinterpret_cast<float2*>(smem + SM::x_off);
+  float2* s_fft = reinterpret_cast<float2*>(smem + SM::fft_off);
 
   if (a.check_done && a.st->done) return;  // uniform: set only between launches
   const int g = threadIdx.x / TPF;
@@ -214,26 +249,34 @@ row_pass_kernel(RowArgs a) {
     mbar_init(&bar[1], 1);
     mbar_fence_init();
   }
-  __syncthreads();
+  fft_sync<W>();
   if (threadIdx.x == 0) {
-    const float2* srcA = RF ? a.f_d1 : a.f_x;
-    mbar_expect_tx(&bar[0], (uint32_t)(nval * M * 8));
-    for (int r = 0; r < nval; ++r) bulk_g2s(s_a + r * M, srcA + (size_t)(y0 + r) * M, M * 8, &bar[0]);
-    mbar_expect_tx(&bar[1], (uint32_t)(nval * M * 16 + (RF ? 2 * nval * M * 8 : 0)));
-    for (int r = 0; r < nval; ++r) {
-      bulk_g2s(s_dn + r * M, a.dn + (size_t)(y0 + r) * M, M * 16, &bar[1]);
-      if constexpr (RF) {
-        bulk_g2s(s_t1 + r * M, a.f_t1 + (size_t)(y0 + r) * M, M * 8, &bar[1]);
-        bulk_g2s(s_x + r * M, a.f_x + (size_t)(y0 + r) * M, M * 8, &bar[1]);
-      }
+    if constexpr (RF) {
+      mbar_expect_tx(&bar[0], (uint32_t)(nval * M * 8));
+      for (int r = 0; r < nval; ++r) bulk_g2s(s_a + r * M, a.f_d1 + (size_t)(y0 + r) * M, M * 8, &bar[0]);
+    } else {
+      mbar_expect_tx(&bar[0], 0u);  // nothing on this barrier: completes at once
     }
+    mbar_expect_tx(&bar[1], (uint32_t)(nval * M * 16));
+    for (int r = 0; r < nval; ++r) bulk_g2s(s_dn + r * M, a.dn + (size_t)(y0 + r) * M, M * 16, &bar[1]);
   }
+  if constexpr (RF) {
+    gather_tiled_rows<M, NT>(s_t1, a.f_t1, y0, nval, a.ny);
+    gather_tiled_rows<M, NT>(s_x, a.f_x, y0, nval, a.ny);
+  } else {
+    gather_tiled_rows<M, NT>(s_a, a.f_x, y0, nval, a.ny);
+  }
+  cp_async_commit();
+
   auto give_up = [&]() {
     if (threadIdx.x == 0) atomicOr(&a.st->err, WF_ERR_TIMEOUT);
     mbar_wait(&bar[0], 0, WF_WAIT_TRIES);
     mbar_wait(&bar[1], 0, WF_WAIT_TRIES);
+    cp_async_wait<0>();
   };
-  if (__syncthreads_or(!mbar_wait(&bar[0], 0, WF_WAIT_TRIES))) {
+  bool ok = mbar_wait(&bar[0], 0, WF_WAIT_TRIES);
+  if constexpr (!RF) cp_async_wait<0>();
+  if (__syncthreads_or(!ok)) {
     give_up();
     return;
   }
@@ -242,8 +285,8 @@ row_pass_kernel(RowArgs a) {
   const float T2 = a.st->Tf[2];
 #pragma unroll
   for (int m = 0; m < E; ++m) v[m] = s_a[g * M + t + m * TPF];
-  c2r_pre<M, E>(v, sb, t, a.twx);
-  fft_block<M, E, true>(v, sb, t, a.twx, 2);
+  c2r_pre<M, E, W>(v, sb, t, a.twx);
+  fft_block<M, E, true, W>(v, sb, t, a.twx, 2);
   if (__syncthreads_or(!mbar_wait(&bar[1], 0, WF_WAIT_TRIES))) {
     give_up();
     return;
@@ -254,13 +297,17 @@ row_pass_kernel(RowArgs a) {
     const float4 q = s_dn[g * M + t + m * TPF];
     v[m] = make_float2(tpx_update(q.x, q.y, v[m].x, T2), tpx_update(q.z, q.w, v[m].y, T2));
   }
-  fft_block<M, E, false>(v, sb, t, a.twx, 2);
-  r2c_post<M, E>(v, sb, t, a.twx);
+  fft_block<M, E, false, W>(v, sb, t, a.twx, 2);
+  r2c_post<M, E, W>(v, sb, t, a.twx);
+  if constexpr (RF) {
+    cp_async_wait<0>();
+    fft_sync<W>();
+  }
   if (!valid) return;
   const size_t row0 = (size_t)y * M;
   if constexpr (!RF) {
 #pragma unroll
-    for (int m = 0; m < E; ++m) a.f_y[row0 + t + m * TPF] = v[m];
+    for (int m = 0; m < E; ++m) a.f_y[tidx(y, t + m * TPF, a.ny)] = v[m];
   } else {
     // eqs. (2mess_d0), (2mess_t0) analogues in the stripe basis
     const float T1 = a.st->Tf[1];
@@ -287,14 +334,14 @@ row_pass_kernel(RowArgs a) {
         t1 = make_float2(fmaf(wb, xo.x - d1.x, d1.x), fmaf(wb, xo.y - d1.y, d1.y));
       }
       a.f_d1[row0 + k] = d1;
-      a.f_t1[row0 + k] = t1;
+      a.f_t1[tidx(y, k, a.ny)] = t1;
     }
   }
 }
 
 template <int M, int MODE>
 static int launch_row_pass(const RowArgs& a, cudaStream_t s) {
-  using Cfg = RowCfg<M>;
+  using Cfg = RowPassCfg<M>;
   constexpr size_t bytes = RowPassSmem<M, MODE>::bytes;
   static bool configured = false;  // per instantiation
   if (!configured) {

@@ -49,7 +49,7 @@ def test_host_only_entry_points(lib):
     assert list(p.theta) == [0.9, 0.9, 1.0]
     assert p.split_f == 0.5 and p.split_fp == 0.5 and p.split_w == 0.0
     assert p.residual_every == 10 and p.check_every == 8
-    assert p.merge_2df == 1 and p.tol_u_scale == 1.0 and p.refine == 0
+    assert p.merge_2df == 1 and p.tol_u_scale == 1.0 and p.refine == 0 and p.refine_tol_scale == 100.0
 
 
 @pytest.mark.parametrize("ny,nx,parts,code", [
@@ -88,5 +88,5 @@ def test_schedule_struct_layout_matches_header(lib):
     from paper_1704_00865_gb300 import wf
     # int, ptr, ptr, int, 4 doubles on LP64
     assert C.sizeof(wf.wf_schedule) == 4 + 4 + 8 + 8 + 4 + 4 + 32
-    assert C.sizeof(wf.wf_params) == 24 + 24 + 8 + 16 + 16
+    assert C.sizeof(wf.wf_params) == 24 + 24 + 8 + 16 + 8 + 8 + 8
     assert C.sizeof(wf.wf_stats) == 8 + 8 * 3 + 24 + 8

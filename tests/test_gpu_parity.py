@@ -127,8 +127,8 @@ def test_defect_correction_reaches_closed_form_to_1e4(wf, n):
     # one defect-correction solve removes the FP32 stagnation error
     prob = synth.make_problem(n, n, 21, homogeneous=True, mask_frac=0.0)
     sched = wf.make_schedule("fixed", O.cooling_levels(1e3, 10), [100] * 10)
-    s, st = _solve_refined(wf, prob, sched, 1e-5, 1, residual_every=10, max_iters=400000,
-                           tol_u_scale=30.0)
+    s, st = _solve_refined(wf, prob, sched, 1e-5, 1, residual_every=10, max_iters=100000,
+                           tol_u_scale=20.0)
     assert st["status"] == 0, st
     assert rel(s, O.closed_form(prob)) < 1e-4
 
@@ -138,7 +138,11 @@ def test_defect_correction_reaches_closed_form_to_1e4(wf, n):
 def test_converges_to_dense_cholesky(wf, shape, kw):
     prob = synth.make_problem(*shape, 31, mask_frac=0.06, k_knee=4.0, k_knee_x=4.0, **kw)
     sched = wf.make_schedule("fixed", O.cooling_levels(1e2, 5), [20] * 5)
-    s, st = _solve_refined(wf, prob, sched, 1e-5, 1, residual_every=10, max_iters=400000, tol_u_scale=10.0)
+    # without a 1/f part there is no 1/f white floor to share; half of the
+    # pixel floor then goes to the stripe part instead
+    extra = dict(split_w=0.5) if kw.get("one_over_f") is False else {}
+    s, st = _solve_refined(wf, prob, sched, 1e-5, 1, residual_every=10, max_iters=100000, tol_u_scale=20.0,
+                           **extra)
     assert st["status"] == 0, st
     assert rel(s, O.dense_wf(prob)) < 1e-4
 
@@ -181,10 +185,12 @@ def test_full_size_three_part_masked_workload(wf):
     s_ref = O.pcg_wf(prob, P=P, tol=1e-10)
     err = rel(s, s_ref)
     print(f"1024^2: {st['iters']} iterations, literal residual {lit:.2e}, rel L2 vs oracle {err:.2e}")
-    assert err < 2e-3
-    # with one defect-correction solve the same workload meets rel L2 <= 1e-4
-    s2, st2 = _solve_refined(wf, prob, sched, 1e-5, 1, residual_every=10, max_iters=200000,
-                             tol_u_scale=50.0)
+    # the stop test targets the residual; slow (low-k stripe and masked)
+    # modes carry a larger share of the error than of the residual
+    assert err < 5e-3
+    # run to the FP32 floor, then one defect-correction solve (tol = 0: each
+    # solve runs exactly max_iters iterations): rel L2 <= 1e-4
+    s2, st2 = _solve_refined(wf, prob, sched, 0.0, 1, residual_every=50, max_iters=40000)
     assert st2["status"] == 0, st2
     lit2 = O.literal_residual(prob, s2, P=P, tol=1e-10)
     err2 = rel(s2, s_ref)
