@@ -37,24 +37,48 @@ import numpy as np  # noqa: E402
 # ---------------------------------------------------------------- workload
 N = 1024
 SEED = 1000
-# Stop test: ||(S^-1 s)_masked|| / ||S^-1 s|| <= TOL and ||Delta d_u|| / ||d_u||
-# <= TOL * TOL_U_SCALE.  Calibrated against the FP64 oracle's literal residual
-# || (S^-1 + N^-1) s - N^-1 d || / || N^-1 d || on this workload, which follows
-# ~ sqrt((0.011 rel_u)^2 + (0.55 rel_m)^2): these values give <= ~8e-6 < 1e-5.
+# Stop test of the first solve: ||(S^-1 s)_masked|| / ||S^-1 s|| <= TOL and
+# ||Delta d_u|| / ||d_u|| <= TOL * TOL_U_SCALE.  Calibrated against the FP64
+# oracle's literal residual || (S^-1 + N^-1) s - N^-1 d || / || N^-1 d || on
+# this workload, which follows ~ sqrt((0.011 rel_u)^2 + (0.55 rel_m)^2):
+# these values give <= ~8e-6 < 1e-5.
 TOL = 1e-5
 TOL_U_SCALE = 50.0
-# cooling schedule: lambda = 10 for 3000 sweeps, then lambda = 1 to the stop
-# test (the fastest of the fixed schedules tried on this workload)
-SCHED_LEVELS_LAM = [10.0]
-SCHED_LEVELS_ITERS = [3000]
+# cooling schedule: lambda = 30, 10, 3, 1.5 for 1000, 2000, 2000, 2000
+# sweeps, then lambda = 1 to the stop test
+SCHED_LEVELS_LAM = [30.0, 10.0, 3.0, 1.5]
+SCHED_LEVELS_ITERS = [1000, 2000, 2000, 2000]
+# The residual test passes while slow modes (low-k_x stripe modes, masked
+# discs) still carry a relative error of a few 1e-3 against the exact filter;
+# one defect-correction solve of REFINE_MAX_ITERS sweeps (unmasked data
+# residual plus masked-pixel source; the cooling levels, then the last
+# REFINE_LAM1_ITERS sweeps at lambda = 1) brings s within 1e-4 of it
+# (measured: 5.1e-5, literal residual 1.1e-6).
+REFINE = 1
+REFINE_MAX_ITERS = 4000
+REFINE_LAM1_ITERS = 500
 RESIDUAL_EVERY = 50
 CHECK_EVERY = 8
 MAX_ITERS = 400000
 SPLIT_F = 0.5           # 1/f white floor carried by the stripe part
 SPLIT_FP = 0.5          # 1/f white floor carried by the white part
-# iterations per solve of this seeded workload (the count wf_solve reports;
-# the reference arm scales its per-iteration time by it)
-ITERS_PER_SOLVE = None
+# sweeps per solve of this seeded workload (first solve + correction, as
+# wf_solve reports them on a GB300); the reference arm scales its measured
+# FP64 time per sweep by it
+ITERS_PER_SOLVE = 15150
+
+
+def solver_params(wf):
+    """wf_params of the benchmark's solve."""
+    return wf.make_params(residual_every=RESIDUAL_EVERY, max_iters=MAX_ITERS, check_every=CHECK_EVERY,
+                          merge_2df=1, split_f=SPLIT_F, split_fp=SPLIT_FP, tol_u_scale=TOL_U_SCALE,
+                          refine=REFINE, refine_max_iters=REFINE_MAX_ITERS,
+                          refine_lam1_iters=REFINE_LAM1_ITERS, refine_tol_scale=1.0)
+
+
+def solver_schedule(wf):
+    return wf.make_schedule("fixed", list(SCHED_LEVELS_LAM), list(SCHED_LEVELS_ITERS))
+
 
 METRIC = "WF solves/sec to rel. residual 1e-5 at 1024^2 3-noise; % HBM roofline"
 UNIT = "solves/s"
@@ -70,7 +94,9 @@ def workload_config():
             "schedule": {"kind": "fixed", "lam": SCHED_LEVELS_LAM, "iters": SCHED_LEVELS_ITERS,
                          "then": "lambda=1 to tol"},
             "stop": {"tol_masked": TOL, "tol_unmasked": TOL * TOL_U_SCALE,
-                     "literal_residual_target": 1e-5},
+                     "literal_residual_target": 1e-5, "rel_error_target": 1e-4},
+            "refine": {"solves": REFINE, "sweeps_each": REFINE_MAX_ITERS,
+                       "of_which_at_lambda_1": REFINE_LAM1_ITERS},
             "params": {"merge_2df": 1, "split_f": SPLIT_F, "split_fp": SPLIT_FP, "theta": [0.9, 0.9, 1.0]},
             "residual_every": RESIDUAL_EVERY,
             "l2": "flushed between steps (512 MiB write), outside the timed events"}
@@ -187,17 +213,20 @@ def _dist():
     return ws, rank, local
 
 
-def _oracle_iter_time(prob, iters, workers=1):
+def _oracle_sweeps(prob, workers, min_sweeps=3, min_seconds=0.0):
+    """Mean seconds per FP64 oracle sweep (merged block, the benchmark's
+    splits), at least `min_sweeps` sweeps and `min_seconds` of work."""
     import oracle as O
     O.set_workers(workers)
-    lv, its = schedule_levels()
+    lv, _ = schedule_levels()
     P = O.build_parts(prob, merge_2df=True, split_f=SPLIT_F, split_fp=SPLIT_FP)
     ch = O.Chain(P)
     ch.sweep(lv[0])  # warm the FFT plans
-    t = time.perf_counter()
-    for _ in range(iters):
+    n, t = 0, time.perf_counter()
+    while n < min_sweeps or time.perf_counter() - t < min_seconds:
         ch.sweep(lv[0])
-    return (time.perf_counter() - t) / iters
+        n += 1
+    return (time.perf_counter() - t) / n, n
 
 
 def run_reference(args):
@@ -205,20 +234,22 @@ def run_reference(args):
     if rank != 0:
         return 0
     prob = problem()
-    per_step_iters = 4
+    cores = os.cpu_count() or 1
+    per_step = 4
     for _ in range(args.warmup):
-        _oracle_iter_time(prob, 1)
-    times = [_oracle_iter_time(prob, per_step_iters) for _ in range(args.steps)]
+        _oracle_sweeps(prob, cores, 1)
+    times = [_oracle_sweeps(prob, cores, per_step)[0] for _ in range(args.steps)]
     t_iter = statistics.mean(times)
     ips = ITERS_PER_SOLVE
     value = (1.0 / (t_iter * ips)) if ips else None
-    sample = (f"{per_step_iters} oracle sweeps of the {N}^2 three-part solve per step, {args.steps} steps; "
-              f"solves/s = 1/(t_iter x {ips} iterations per solve of this seeded workload)")
+    sample = (f"{per_step} FP64 oracle sweeps of the {N}^2 three-part solve per step (scipy.fft with "
+              f"{cores} workers), {args.steps} steps; solves/s = 1/(s per sweep x {ips} sweeps per solve, "
+              f"the count of the GPU solve of this seeded workload)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t_iter * (ips or 0) * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
                              "s_per_iter": t_iter},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -247,11 +278,8 @@ def run_gpu(args):
     d2h = out_h.numel() * out_h.element_size()
     flush = torch.empty(512 * 1024 * 1024 // 4, device="cuda")
 
-    params = wf.make_params(residual_every=RESIDUAL_EVERY, max_iters=MAX_ITERS, check_every=CHECK_EVERY,
-                            merge_2df=1, split_f=SPLIT_F, split_fp=SPLIT_FP, tol_u_scale=TOL_U_SCALE)
-    plan = wf.Plan(N, N, wf.parts_of(prob), params)
-    lv, its = schedule_levels()
-    sched = wf.make_schedule("fixed", lv, its)
+    plan = wf.Plan(N, N, wf.parts_of(prob), solver_params(wf))
+    sched = solver_schedule(wf)
     stream = torch.cuda.current_stream()
 
     def step(inp, out):
@@ -321,12 +349,16 @@ def run_gpu(args):
     iters = [s["iters"] for s in stats]
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        t_iter = _oracle_iter_time(prob, 3)
+        cores = os.cpu_count() or 1
         ips = statistics.median(iters)
-        cpu = {"value": 1.0 / (t_iter * ips), "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"3 FP64 oracle sweeps of this {N}^2 solve (numpy/scipy, 1 thread), "
-                         f"{t_iter:.3f} s/iteration, scaled by the {ips:.0f} iterations per solve measured here",
-               "s_per_iter": t_iter}
+        t_all, n_all = _oracle_sweeps(prob, cores, 3, 8.0)
+        t_one, n_one = _oracle_sweeps(prob, 1, 3, 4.0)
+        cpu = {"value": 1.0 / (t_all * ips), "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{n_all} FP64 oracle sweeps of this {N}^2 solve (scipy.fft, {cores} workers; "
+                         f"elementwise numpy on one thread), {t_all:.3f} s/sweep, scaled by the {ips:.0f} "
+                         f"sweeps per solve measured here",
+               "s_per_iter": t_all,
+               "single_core": {"value": 1.0 / (t_one * ips), "s_per_iter": t_one, "sweeps": n_one}}
     cfg = workload_config()
     cfg.update({"iters_per_solve": iters[0] if len(set(iters)) == 1 else iters,
                 "final_rel_rho_u": stats[-1]["rel_rho_u"], "final_rel_rho_m": stats[-1]["rel_rho_m"],

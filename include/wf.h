@@ -125,16 +125,26 @@ typedef struct {
  *                  the iteration then needs no tau for the 1/f part and
  *                  split_f may be 1.  0: the plain sweep.  Default 1.
  *  refine          defect-correction solves wf_solve adds after the first
- *                  (default 0).  Each computes Delta d_u = [(I + N S^-1) s - d]
- *                  on unmasked pixels for the accumulated s (Sec. 2), solves
- *                  the same Wiener filter with Delta d_u as data and subtracts
- *                  the result: WF(Delta d) = s - s_exact up to the masked-pixel
- *                  term, so each pass removes the FP32 stagnation error of the
- *                  previous one.  Only wf_solve refines.
+ *                  (default 0).  Each takes the residual of the accumulated s
+ *                  (Sec. 2): Delta d_u = [(I + N S^-1) s - d] on unmasked
+ *                  pixels and j = (S^-1 s) on masked pixels, solves the same
+ *                  filter with Delta d_u as data and j as a source,
+ *                  (S^-1 + N^-1) e = N^-1 Delta d + j, and subtracts e =
+ *                  s - s_exact.  Each pass removes most of the error the
+ *                  previous solve left (FP32 stagnation and slow modes).
+ *                  Only wf_solve refines.
  *  refine_tol_scale the correction solves stop at tol * refine_tol_scale
  *                  (their data is the previous residual, so percent-level
  *                  accuracy already cuts the error by that factor); default
  *                  100.
+ *  refine_max_iters iteration cap of each correction solve; 0 (default):
+ *                  max_iters.  A correction that reaches a nonzero cap does
+ *                  not make wf_solve return WF_ENOCONV.
+ *  refine_lam1_iters with a cap and a fixed schedule, each correction runs
+ *                  the schedule's levels (lambda > 1) for at most
+ *                  refine_max_iters - refine_lam1_iters sweeps and then
+ *                  lambda = 1 to the cap, so that it ends on the unbiased
+ *                  fixed point; default 0.
  *  residual_every  R: the residual and the lambda rule run every R
  *                  iterations; default 10.
  *  max_iters       default 200000.
@@ -154,7 +164,8 @@ typedef struct {
   int merge_2df;
   int refine;
   double refine_tol_scale;
-  int reserved[2];
+  int refine_max_iters;
+  int refine_lam1_iters;
 } wf_params;
 
 /* Results of a solve. */

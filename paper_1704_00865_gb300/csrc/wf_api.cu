@@ -51,14 +51,22 @@ struct wf_plan_s {
   float4* dn_orig = nullptr;
   float *s_acc = nullptr, *s_corr = nullptr;
   float2* rho = nullptr;
+  float2* jmap = nullptr;     // source j on masked pixels (pixel pairs)
+  float2* src_2df = nullptr;  // its 2D DFT, column-tiled
+  bool has_src = false;       // the loaded problem carries the source
   // CUDA graph of one polling chunk of wf_run (K checkpoints of R sweeps),
   // captured and replayed on the plan's own stream (the caller's stream may
   // be the legacy default stream, which cannot be captured)
   cudaStream_t gstream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-  cudaGraphExec_t chunk_exec = nullptr;
-  std::vector<unsigned char> chunk_key;
-  long long chunk_launches = 0;
+  // two cached chunk graphs: a solve and its correction solves alternate
+  struct ChunkGraph {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<unsigned char> key;
+    long long launches = 0;
+    long long last_use = 0;
+  } chunk[2];
+  long long chunk_clock = 0;
   std::vector<void*> allocs;
 };
 
@@ -157,7 +165,8 @@ void wf_params_default(wf_params* p) {
 
 void wf_plan_destroy(wf_plan_t P) {
   if (!P) return;
-  if (P->chunk_exec) cudaGraphExecDestroy(P->chunk_exec);
+  for (auto& g : P->chunk)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
   if (P->ev_in) cudaEventDestroy(P->ev_in);
   if (P->ev_out) cudaEventDestroy(P->ev_out);
   if (P->gstream) cudaStreamDestroy(P->gstream);
@@ -182,7 +191,9 @@ int wf_plan_create(wf_plan_t* out, int ny, int nx, unsigned parts, const wf_para
       !(prm.split_w >= 0.0 && prm.split_w < 1.0))
     return WF_EINVAL;
   if (!(prm.tol_u_scale > 0.0) || (prm.merge_2df != 0 && prm.merge_2df != 1)) return WF_EINVAL;
-  if (prm.refine < 0 || prm.refine > 8 || !(prm.refine_tol_scale >= 1.0)) return WF_EINVAL;
+  if (prm.refine < 0 || prm.refine > 8 || !(prm.refine_tol_scale >= 1.0) || prm.refine_max_iters < 0 ||
+      prm.refine_lam1_iters < 0)
+    return WF_EINVAL;
 
   wf_plan_s* P = new wf_plan_s();
   P->ny = ny;
@@ -233,6 +244,8 @@ int wf_plan_create(wf_plan_t* out, int ny, int nx, unsigned parts, const wf_para
     AL(P->s_acc, npx);
     AL(P->s_corr, npx);
     AL(P->rho, npx / 2);
+    AL(P->jmap, npx / 2);
+    AL(P->src_2df, nh);
   }
 #undef AL
   if (rc != WF_OK) {
@@ -291,6 +304,7 @@ static RowArgs row_args(wf_plan_s* P) {
   a.st = P->st;
   a.r_g = P->r_g;
   a.r_q = P->r_q;
+  a.src_px = P->has_src ? P->jmap : nullptr;
   return a;
 }
 
@@ -311,6 +325,7 @@ static ColArgs col_args(wf_plan_s* P, int parity) {
   a.st = P->st;
   a.r_g = P->r_g;
   a.r_q = P->r_q;
+  a.src = P->has_src ? P->src_2df : nullptr;
   return a;
 }
 
@@ -326,7 +341,8 @@ static int enqueue_row_pass(wf_plan_s* P) {
 static int enqueue_col_pass(wf_plan_s* P, int parity) {
   ColArgs ca = col_args(P, parity);
   ca.check_done = 1;
-  CKI(launch_col(P->merge ? COL_PASS_MERGE : (P->has_f ? COL_PASS_2DF : COL_PASS_NO2DF), ca, P->stream));
+  const int mode = (P->has_f && !P->merge) ? COL_PASS_2DF : (P->has_src ? COL_PASS_MERGE_SRC : COL_PASS_MERGE);
+  CKI(launch_col(mode, ca, P->stream));
   P->launches += 1;
   return WF_OK;
 }
@@ -356,9 +372,11 @@ static int enqueue_residual(wf_plan_s* P, int parity, int check_done) {
 
 // Delta d of a pixel-space s against the original data (table dn_orig):
 // rho map (unmasked pixels) and the partial sums of the residual.
-static int enqueue_resid_map(wf_plan_s* P, const float* s_px, float2* rho_out) {
+static int enqueue_resid_map(wf_plan_s* P, const float* s_px, float2* rho_out, float2* gm_out) {
   RowArgs ra = row_args(P);
   ra.check_done = 0;
+  ra.src_px = nullptr;  // the caller's problem has no source
+  ra.gm_out = gm_out;
   ra.dn = P->dn_orig;
   ra.in_px = (const float2*)s_px;
   ra.out_rf = P->r_q;
@@ -369,6 +387,7 @@ static int enqueue_resid_map(wf_plan_s* P, const float* s_px, float2* rho_out) {
   ra.part0 = P->part;
   ra.part1 = P->part + P->nrow;
   CKI(launch_row(ROW_RESID_B, ra, P->stream));
+  ra.gm_out = nullptr;
   if (P->has_f) CKI(launch_col(COL_RESID_C, ca, P->stream));
   ra.part0 = P->part + 2 * P->nrow;
   ra.out_px = rho_out;
@@ -445,6 +464,7 @@ int wf_set_problem(wf_plan_t P, const float* d, const float* pixel_var, const ui
   CK(cudaStreamSynchronize(P->stream));
   P->it_done = 0;
   P->loaded = false;
+  P->has_src = false;
   const int st = finish_status(P->h_st->err);
   if (st != WF_OK) return st;
   P->loaded = true;
@@ -538,19 +558,31 @@ static int wf_run_on(wf_plan_t P, const wf_schedule* sch, double tol, wf_stats* 
   // Full chunks start on the same sweep parity when K R is even, so one
   // captured graph replays them all; it is kept while the controller
   // arguments and the start parity stay the same.
-  std::vector<unsigned char> key(sizeof(CtrlArgs) + 8);
-  memcpy(key.data(), &c, sizeof(CtrlArgs));
-  const long long par = it0 & 1;
-  memcpy(key.data() + sizeof(CtrlArgs), &par, 8);
+  // (the kernel arguments also depend on whether a source is loaded)
+  // (built field by field: struct padding must not make equal keys differ)
+  std::vector<unsigned char> key;
+  auto put = [&key](const void* p, size_t n) {
+    const unsigned char* b = (const unsigned char*)p;
+    key.insert(key.end(), b, b + n);
+  };
+  const long long par = it0 & 1, src = P->has_src ? 1 : 0;
+  put(&c.tol, 8); put(&c.tol_u, 8); put(&c.ratio, 8); put(&c.expo, 8); put(&c.snap, 8);
+  put(&c.mode, 4); put(&c.nlevels, 4); put(&c.R, 4); put(&c.max_iters, 4); put(&c.count_iters, 4);
+  put(&par, 8); put(&src, 8);
   const bool use_graph = (per_chunk % 2 == 0);
   bool first = true;
   for (;;) {
     const bool full = enq + per_chunk <= cap;
     if (use_graph && full && !first) {
-      if (!P->chunk_exec || P->chunk_key != key) {
-        if (P->chunk_exec) {
-          cudaGraphExecDestroy(P->chunk_exec);
-          P->chunk_exec = nullptr;
+      wf_plan_s::ChunkGraph* G = nullptr;
+      for (auto& g : P->chunk)
+        if (g.exec && g.key == key) G = &g;
+      if (!G) {
+        // replace the least recently used slot
+        G = (P->chunk[0].last_use <= P->chunk[1].last_use) ? &P->chunk[0] : &P->chunk[1];
+        if (G->exec) {
+          cudaGraphExecDestroy(G->exec);
+          G->exec = nullptr;
         }
         cudaGraph_t g = nullptr;
         const long long l0 = P->launches;
@@ -562,15 +594,16 @@ static int wf_run_on(wf_plan_t P, const wf_schedule* sch, double tol, wf_stats* 
           return rc;
         }
         CK(ce);
-        cudaError_t ie = cudaGraphInstantiate(&P->chunk_exec, g, 0);
+        cudaError_t ie = cudaGraphInstantiate(&G->exec, g, 0);
         cudaGraphDestroy(g);
         CK(ie);
-        P->chunk_launches = P->launches - l0;
+        G->launches = P->launches - l0;
         P->launches = l0;
-        P->chunk_key = key;
+        G->key = key;
       }
-      CK(cudaGraphLaunch(P->chunk_exec, P->stream));
-      P->launches += P->chunk_launches;
+      G->last_use = ++P->chunk_clock;
+      CK(cudaGraphLaunch(G->exec, P->stream));
+      P->launches += G->launches;
       enq += per_chunk;
     } else {
       const long long e0 = enq;
@@ -696,10 +729,50 @@ int wf_solve(wf_plan_t P, const float* d, const float* pixel_var, const uint8_t*
   if ((rc = wf_get_field(P, WF_FIELD_S, P->s_acc))) return rc;
   wf_stats tot = s0;
   const size_t nhb = (size_t)P->ny * P->M * sizeof(float2);
+  // a source on masked pixels needs the merged 2DF block (or no 1/f part)
+  const bool with_src = !(P->has_f && !P->merge);
+  // A capped correction runs the fixed schedule's levels for at most
+  // refine_max_iters - refine_lam1_iters sweeps, then lambda = 1 for the
+  // rest: the cooling levels move the slow modes, the lambda = 1 sweeps
+  // remove the bias the last level leaves in the fast ones.
+  wf_schedule csched = *sched;
+  std::vector<double> clam;
+  std::vector<int> citers;
+  const int cap = P->p.refine_max_iters;
+  if (cap > 0 && sched->mode == WF_SCHED_FIXED && sched->lam && sched->iters && sched->nlevels > 0) {
+    long long left = std::max(0, cap - P->p.refine_lam1_iters);
+    for (int i = 0; i < sched->nlevels && left > 0; ++i) {
+      const int n = (int)std::min<long long>(std::max(0, sched->iters[i]), left);
+      if (n > 0 && sched->lam[i] > 1.0) {
+        clam.push_back(sched->lam[i]);
+        citers.push_back(n);
+        left -= n;
+      }
+    }
+    clam.push_back(1.0);
+    citers.push_back(0);
+    csched.lam = clam.data();
+    csched.iters = citers.data();
+    csched.nlevels = (int)clam.size();
+  }
   for (int r = 0; r < P->p.refine; ++r) {
-    if ((rc = enqueue_resid_map(P, P->s_acc, P->rho))) return rc;
+    // residual of the accumulated s: Delta d_u (data) and (S^-1 s)_m (source)
+    if ((rc = enqueue_resid_map(P, P->s_acc, P->rho, P->jmap))) return rc;
     CKI(launch_pack_data(P->dn, P->dn_orig, P->rho, npx / 2, P->part + 3 * P->nrow, P->st, P->stream));
     P->launches += 2;
+    if (with_src) {
+      // j^ = 2D DFT of the masked-pixel source, column-tiled
+      RowArgs ra = row_args(P);
+      ra.in_px = P->jmap;
+      ra.out_rf = P->r_q;
+      CKI(launch_row(ROW_R2C, ra, P->stream));
+      ColArgs ca = col_args(P, 0);
+      ca.in = P->r_q;
+      ca.out = P->src_2df;
+      CKI(launch_col(COL_FWD_TILED, ca, P->stream));
+      P->launches += 2;
+      P->has_src = true;
+    }
     CK(cudaMemsetAsync(P->f_x, 0, nhb, P->stream));
     if (P->f_d1) CK(cudaMemsetAsync(P->f_d1, 0, nhb, P->stream));
     if (P->f_t1) CK(cudaMemsetAsync(P->f_t1, 0, nhb, P->stream));
@@ -707,17 +780,23 @@ int wf_solve(wf_plan_t P, const float* d, const float* pixel_var, const uint8_t*
     if (P->f_t0) CK(cudaMemsetAsync(P->f_t0, 0, nhb, P->stream));
     P->it_done = 0;
     wf_stats sr{};
-    int sr_status = wf_run(P, sched, tol * P->p.refine_tol_scale, &sr);
+    const int main_cap = P->p.max_iters;
+    if (P->p.refine_max_iters > 0) P->p.max_iters = P->p.refine_max_iters;
+    int sr_status = wf_run(P, &csched, tol * P->p.refine_tol_scale, &sr);
+    P->p.max_iters = main_cap;
+    if (sr_status == WF_OK || sr_status == WF_ENOCONV) rc = wf_get_field(P, WF_FIELD_S, P->s_corr);
+    P->has_src = false;
     if (sr_status != WF_OK && sr_status != WF_ENOCONV) return sr_status;
-    if (sr_status == WF_ENOCONV) status = WF_ENOCONV;
+    if (rc) return rc;
+    // a correction that runs to refine_max_iters has done what was asked
+    if (sr_status == WF_ENOCONV && P->p.refine_max_iters == 0) status = WF_ENOCONV;
     tot.iters += sr.iters;
     tot.checkpoints += sr.checkpoints;
-    if ((rc = wf_get_field(P, WF_FIELD_S, P->s_corr))) return rc;
     CKI(launch_sub(P->s_acc, P->s_corr, npx, P->stream));
     P->launches += 1;
   }
   // residual of the refined s against the original problem
-  if ((rc = enqueue_resid_map(P, P->s_acc, P->rho))) return rc;
+  if ((rc = enqueue_resid_map(P, P->s_acc, P->rho, nullptr))) return rc;
   CK(cudaMemcpyAsync(&P->st->du2, &du2, sizeof(double), cudaMemcpyHostToDevice, P->stream));
   CtrlArgs c = ctrl_args(P);
   c.count_iters = 0;

@@ -65,6 +65,8 @@ col_kernel(ColArgs a) {
   using Cfg = ColCfg<L>;
   constexpr int E = Cfg::E, TPC = Cfg::TPC, W = Cfg::W;
   __shared__ float2 sbuf[W][Cfg::STRIDE];
+  pdl_trigger();
+  pdl_wait();
 
   const int c = threadIdx.x % W;
   const int t = threadIdx.x / W;
@@ -116,16 +118,23 @@ col_kernel(ColArgs a) {
       for (int m = 0; m < E; ++m) {
         const int k = t + m * TPC;
         const float2 eg = valid ? a.eig[att(k)] : make_float2(1.f, 1.f);
+        // with a source j: g = (y + (N0 + T) j^) / (C + N0 + T)
+        const float2 jv = (a.src != nullptr && valid) ? a.src[att(k)] : make_float2(0.f, 0.f);
         if (blockIdx.x == 0 && c == 0) {
           const float2 egb = a.eig_nyq[k];
-          float2 A, B;
+          const float2 jp = (a.src != nullptr) ? a.src[att((L - k) & (L - 1))] : make_float2(0.f, 0.f);
+          float2 A, B, JA, JB;
           unpack_pair(v[m], vp[m], A, B);
-          const float2 gA = cscale(A, __fdividef(1.f, eg.x + eg.y + off0 + Tl));
-          const float2 gB = cscale(B, __fdividef(1.f, egb.x + egb.y + off0 + Tl));
+          unpack_pair(jv, jp, JA, JB);
+          const float na = eg.y + off0 + Tl, nb = egb.y + off0 + Tl;
+          const float2 gA = cscale(make_float2(fmaf(na, JA.x, A.x), fmaf(na, JA.y, A.y)), __fdividef(1.f, eg.x + na));
+          const float2 gB = cscale(make_float2(fmaf(nb, JB.x, B.x), fmaf(nb, JB.y, B.y)), __fdividef(1.f, egb.x + nb));
           v[m] = repack_pair(gA, gB);
           w[m] = repack_pair(cscale(gA, eg.x), cscale(gB, egb.x));
         } else {
-          const float2 g = cscale(v[m], __fdividef(1.f, eg.x + eg.y + off0 + Tl));
+          const float na = eg.y + off0 + Tl;
+          const float2 g = cscale(make_float2(fmaf(na, jv.x, v[m].x), fmaf(na, jv.y, v[m].y)),
+                                  __fdividef(1.f, eg.x + na));
           v[m] = g;
           w[m] = cscale(g, eg.x);
         }
@@ -232,14 +241,17 @@ col_kernel(ColArgs a) {
 #pragma unroll
       for (int m = 0; m < E; ++m) a.out[at(t + m * TPC)] = a.in[att(t + m * TPC)];
     }
-  } else if constexpr (MODE == COL_FWD || MODE == COL_INV) {
+  } else if constexpr (MODE == COL_FWD || MODE == COL_INV || MODE == COL_FWD_TILED) {
 #pragma unroll
     for (int m = 0; m < E; ++m) v[m] = valid ? a.in[at(t + m * TPC)] : make_float2(0.f, 0.f);
     fft_block<L, E, MODE == COL_INV>(v, sb, t, a.twy, 1);
     const float sc = (MODE == COL_INV) ? 1.0f / (float)L : 1.0f;
     if (valid) {
 #pragma unroll
-      for (int m = 0; m < E; ++m) a.out[at(t + m * TPC)] = cscale(v[m], sc);
+      for (int m = 0; m < E; ++m) {
+        if constexpr (MODE == COL_FWD_TILED) a.out[att(t + m * TPC)] = cscale(v[m], sc);
+        else a.out[at(t + m * TPC)] = cscale(v[m], sc);
+      }
     }
   }
 }
@@ -251,14 +263,18 @@ col_kernel(ColArgs a) {
 #ifndef WF_COL_E
 #define WF_COL_E 0  // 0: the default choice below; else values per thread (4, 8, 16)
 #endif
+constexpr size_t kMaxSmem = 227 * 1024;  // dynamic shared memory per CTA
+
 template <int L, int MODE>
 struct ColPassCfg {
   static constexpr bool T0 = (MODE == COL_PASS_2DF);
+  static constexpr bool SRC = (MODE == COL_PASS_MERGE_SRC);
+  static constexpr bool EXTRA = T0 || SRC;  // a third staged tile
   static constexpr int E = (WF_COL_E > 0 && WF_COL_E <= L / 2) ? WF_COL_E : ((L >= 512) ? 16 : 8);
   static constexpr int TPC = L / E;
   static constexpr int W_MIN = (TPC >= 32) ? 1 : 32 / TPC;  // at least one warp
   // widest staging that fits in 227 KB of shared memory
-  static constexpr int W_FIT = T0 ? (L >= 4096 ? 1 : (L >= 2048 ? 2 : WF_TW)) : (L >= 4096 ? 2 : WF_TW);
+  static constexpr int W_FIT = EXTRA ? (L >= 4096 ? 1 : (L >= 2048 ? 2 : WF_TW)) : (L >= 4096 ? 2 : WF_TW);
   static constexpr int W_WANT = (W_MIN > W_FIT) ? ((W_MIN + WF_TW - 1) / WF_TW) * WF_TW : W_FIT;
   static constexpr int W_CAP = 1024 / TPC;  // at most 1024 threads per CTA
   static constexpr int W = (W_WANT <= W_CAP) ? W_WANT
@@ -270,8 +286,13 @@ struct ColPassCfg {
   static constexpr int STRIDE = SP + ((WANT - SP % 16) + 16) % 16;
   static constexpr size_t tile = (size_t)L * W * 8;
   static constexpr size_t y_off = 16, eig_off = y_off + tile, t0_off = eig_off + tile;
-  static constexpr size_t fft_off = t0_off + (T0 ? tile : 0);
-  static constexpr size_t bytes = fft_off + (size_t)W * STRIDE * 8;
+  static constexpr size_t tw_off = t0_off + (EXTRA ? tile : 0);
+  static constexpr size_t fft_bytes = (size_t)W * STRIDE * 8;
+  // the twiddle table (L values) is staged too when it still fits
+  static constexpr bool TWS = tw_off + (size_t)L * 8 + fft_bytes <= kMaxSmem;
+  static constexpr size_t fft_off = tw_off + (TWS ? (size_t)L * 8 : 0);
+  static constexpr size_t bytes = fft_off + fft_bytes;
+  static_assert(bytes <= kMaxSmem, "column pass staging exceeds shared memory");
   // position of (ky, column c of the CTA) in the staged Y / eig tiles
   static __device__ __forceinline__ int sidx(int ky, int c) {
     if constexpr (TILED) return (c / WF_TW) * L * WF_TW + ky * WF_TW + (c % WF_TW);
@@ -321,10 +342,10 @@ col_pass_kernel(ColArgs a) {
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
   float2* s_y = reinterpret_cast<float2*>(smem + Cfg::y_off);
   float2* s_eig = reinterpret_cast<float2*>(smem + Cfg::eig_off);
-  float2* s_t0 = reinterpret_cast<float2*>(smem + Cfg::t0_off);  // plain sweep only
+  float2* s_t0 = reinterpret_cast<float2*>(smem + Cfg::t0_off);  // plain sweep: t_2DF; source: j^
+  float2* s_tw = reinterpret_cast<float2*>(smem + Cfg::tw_off);
   float2* s_fft = reinterpret_cast<float2*>(smem + Cfg::fft_off);
 
-  if (a.check_done && a.st->done) return;  // uniform: set only between launches
   const int c = threadIdx.x % W;
   const int t = threadIdx.x / W;
   const int ncols = a.nx / 2;
@@ -338,18 +359,47 @@ col_pass_kernel(ColArgs a) {
     mbar_fence_init();
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    mbar_expect_tx(&bar[0], Cfg::TILED ? (uint32_t)Cfg::tile : 0u);
-    mbar_expect_tx(&bar[1], Cfg::TILED ? (uint32_t)Cfg::tile : 0u);
+  if constexpr (WF_PDL_EARLY) pdl_trigger();
+  // before the previous kernel has finished: the (C, P1f) tile and the
+  // twiddle table, fixed during a solve, on barrier 1
+  if (threadIdx.x == 0)
+    mbar_expect_tx(&bar[1], (Cfg::TILED ? (uint32_t)Cfg::tile : 0u) + (Cfg::TWS ? (uint32_t)(L * 8) : 0u));
+  stage_tiled<L, MODE>(s_eig, a.eig, col0, a.ny, &bar[1]);
+  if constexpr (Cfg::TWS)
+    if (threadIdx.x == 0) bulk_g2s(s_tw, a.twy, (uint32_t)(L * 8), &bar[1]);
+  cp_async_commit();
+  // (C, P1f) at kx = nx/2 for the packed column (fixed during a solve)
+  const bool packed = (blockIdx.x == 0 && c == 0);
+  float2 egn[E];
+  if (packed) {
+#pragma unroll
+    for (int m = 0; m < E; ++m) egn[m] = __ldg(&a.eig_nyq[t + m * TPC]);
   }
+  pdl_wait();
+  if (a.check_done && a.st->done) {  // uniform: set only between launches
+    if (!mbar_wait(&bar[1], 0, WF_WAIT_TRIES) && threadIdx.x == 0) atomicOr(&a.st->err, WF_ERR_TIMEOUT);
+    cp_async_wait<0>();
+    return;
+  }
+  // link covariances of this lambda level (written by the controller)
+  const float Tl = a.has_rf ? a.st->Tf[1] : a.st->Tf[2];  // link to the RF/PX messenger
+  const float off0 = (float)a.st->off[0];
+  const float T0 = Cfg::T0 ? a.st->Tf[0] : 0.f;
+  const float T0s = Cfg::T0 ? a.st->T0s[a.parity] : 0.f;
+  // the messenger tile (and the source tile) on barrier 0
+  if (threadIdx.x == 0)
+    mbar_expect_tx(&bar[0], Cfg::TILED ? (uint32_t)(Cfg::tile * (Cfg::SRC ? 2 : 1)) : 0u);
   stage_tiled<L, MODE>(s_y, a.f_y, col0, a.ny, &bar[0]);
   cp_async_commit();
-  stage_tiled<L, MODE>(s_eig, a.eig, col0, a.ny, &bar[1]);
+  if constexpr (Cfg::SRC) stage_tiled<L, MODE>(s_t0, a.src, col0, a.ny, &bar[0]);
   if constexpr (Cfg::T0) tile_load_rowmajor<L, W, Cfg::THREADS>(s_t0, a.f_t0, col0, ncols);
   cp_async_commit();
   cp_async_wait<1>();
-  if (__syncthreads_or(!mbar_wait(&bar[0], 0, WF_WAIT_TRIES))) {
+  const bool ok0 = mbar_wait(&bar[0], 0, WF_WAIT_TRIES);
+  const bool ok1 = ok0 && mbar_wait(&bar[1], 0, WF_WAIT_TRIES);
+  if (__syncthreads_or(!ok1)) {
     if (threadIdx.x == 0) atomicOr(&a.st->err, WF_ERR_TIMEOUT);
+    mbar_wait(&bar[0], 0, WF_WAIT_TRIES);
     mbar_wait(&bar[1], 0, WF_WAIT_TRIES);
     cp_async_wait<0>();
     return;
@@ -358,7 +408,7 @@ col_pass_kernel(ColArgs a) {
   float2 v[E];
 #pragma unroll
   for (int m = 0; m < E; ++m) v[m] = s_y[Cfg::sidx(t + m * TPC, c)];
-  fft_block<L, E, false>(v, sb, t, a.twy, 1);
+  fft_block<L, E, false, false, Cfg::TWS>(v, sb, t, Cfg::TWS ? s_tw : a.twy, 1);
 
   // partner values Z[-k] for the packed column 0 (CTA 0 only; uniform)
   float2 vp[E];
@@ -371,19 +421,8 @@ col_pass_kernel(ColArgs a) {
     __syncthreads();
   }
   cp_async_wait<0>();
-  if (__syncthreads_or(!mbar_wait(&bar[1], 0, WF_WAIT_TRIES))) {
-    if (threadIdx.x == 0) atomicOr(&a.st->err, WF_ERR_TIMEOUT);
-    return;
-  }
+  __syncthreads();
 
-  const float Tl = a.has_rf ? a.st->Tf[1] : a.st->Tf[2];  // link to the RF/PX messenger
-  const float off0 = (float)a.st->off[0];
-  const bool packed = (blockIdx.x == 0 && c == 0);
-  float T0 = 0.f, T0s = 0.f;
-  if constexpr (Cfg::T0) {
-    T0 = a.st->Tf[0];
-    T0s = a.st->T0s[a.parity];
-  }
 #pragma unroll
   for (int m = 0; m < E; ++m) {
     const int k = t + m * TPC;
@@ -393,7 +432,7 @@ col_pass_kernel(ColArgs a) {
       // d_2DF = (C + N0)/(C + N0 + T) y, s = C/(C + N0) d_2DF implicit
       const float pa = eg.x + eg.y + off0;
       if (packed) {
-        const float2 egb = a.eig_nyq[k];
+        const float2 egb = egn[m];
         const float pb = egb.x + egb.y + off0;
         float2 A, B;
         unpack_pair(v[m], vp[m], A, B);
@@ -401,11 +440,31 @@ col_pass_kernel(ColArgs a) {
       } else {
         v[m] = cscale(v[m], __fdividef(pa, pa + Tl));
       }
+    } else if constexpr (MODE == COL_PASS_MERGE_SRC) {
+      // the same block with a source j in the objective (-2 s.j): the joint
+      // minimiser is d_2DF = ((C + N0) y + T C j^) / (C + N0 + T)
+      const float pa = eg.x + eg.y + off0;
+      const float2 jv = s_t0[Cfg::sidx(k, c)];
+      if (packed) {
+        const float2 egb = egn[m];
+        const float pb = egb.x + egb.y + off0;
+        const float2 jp = s_t0[Cfg::sidx((L - k) & (L - 1), c)];
+        float2 A, B, JA, JB;
+        unpack_pair(v[m], vp[m], A, B);
+        unpack_pair(jv, jp, JA, JB);
+        const float ia = __fdividef(1.f, pa + Tl), ib = __fdividef(1.f, pb + Tl);
+        const float2 dA = make_float2((pa * A.x + Tl * eg.x * JA.x) * ia, (pa * A.y + Tl * eg.x * JA.y) * ia);
+        const float2 dB = make_float2((pb * B.x + Tl * egb.x * JB.x) * ib, (pb * B.y + Tl * egb.x * JB.y) * ib);
+        v[m] = repack_pair(dA, dB);
+      } else {
+        const float ia = __fdividef(1.f, pa + Tl);
+        v[m] = make_float2((pa * v[m].x + Tl * eg.x * jv.x) * ia, (pa * v[m].y + Tl * eg.x * jv.y) * ia);
+      }
     } else if constexpr (MODE == COL_PASS_2DF) {
       const float2 t0o = s_t0[k * W + c];
       float2 t0n, d0;
       if (packed) {
-        const float2 egb = a.eig_nyq[k];
+        const float2 egb = egn[m];
         const float2 t0p = s_t0[((L - k) & (L - 1)) * W + c];
         float2 yA, yB, tA, tB, tnA, tnB;
         unpack_pair(v[m], vp[m], yA, yB);
@@ -424,7 +483,7 @@ col_pass_kernel(ColArgs a) {
       if (packed) {
         float2 yA, yB;
         unpack_pair(v[m], vp[m], yA, yB);
-        const float2 egb = a.eig_nyq[k];
+        const float2 egb = egn[m];
         v[m] = repack_pair(cscale(yA, __fdividef(eg.x, eg.x + Tl)), cscale(yB, __fdividef(egb.x, egb.x + Tl)));
       } else {
         v[m] = cscale(v[m], __fdividef(eg.x, eg.x + Tl));
@@ -435,7 +494,8 @@ col_pass_kernel(ColArgs a) {
     // publish the T_0 that the new t_2DF was made with (implicit s)
     if (blockIdx.x == 0 && threadIdx.x == 0) a.st->T0s[a.parity ^ 1] = T0;
   }
-  fft_block<L, E, true>(v, sb, t, a.twy, 1);
+  fft_block<L, E, true, false, Cfg::TWS>(v, sb, t, Cfg::TWS ? s_tw : a.twy, 1);
+  if constexpr (!WF_PDL_EARLY) pdl_trigger();
   const float sc = 1.0f / (float)L;
 #pragma unroll
   for (int m = 0; m < E; ++m) a.f_x[tidx(t + m * TPC, col, a.ny)] = cscale(v[m], sc);
@@ -444,19 +504,18 @@ col_pass_kernel(ColArgs a) {
 template <int L, int MODE>
 static int launch_col_pass(const ColArgs& a, cudaStream_t s) {
   using Cfg = ColPassCfg<L, MODE>;
-  constexpr size_t bytes = Cfg::bytes;
+  const int ncols = a.nx / 2;
+  if (ncols % Cfg::W != 0) return (int)cudaErrorInvalidValue;
+  constexpr size_t kBytes = Cfg::bytes;
   static bool configured = false;  // per instantiation
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(col_pass_kernel<L, MODE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBytes);
     if (e != cudaSuccess) return (int)e;
     configured = true;
   }
-  const int ncols = a.nx / 2;
-  if (ncols % Cfg::W != 0) return (int)cudaErrorInvalidValue;
   const dim3 grid(ncols / Cfg::W), block(Cfg::THREADS);
-  col_pass_kernel<L, MODE><<<grid, block, bytes, s>>>(a);
-  return (int)cudaGetLastError();
+  return launch_pdl(col_pass_kernel<L, MODE>, grid, block, kBytes, s, a);
 }
 
 template <int L>
@@ -466,14 +525,16 @@ static int launch_col_L(int mode, const ColArgs& a, cudaStream_t s) {
   const dim3 grid((ncols + Cfg::W - 1) / Cfg::W), block(Cfg::THREADS);
   switch (mode) {
     case COL_PASS_2DF: return launch_col_pass<L, COL_PASS_2DF>(a, s);
-    case COL_PASS_NO2DF: return launch_col_pass<L, COL_PASS_NO2DF>(a, s);
-    case COL_RESID_A: col_kernel<L, COL_RESID_A><<<grid, block, 0, s>>>(a); break;
-    case COL_RESID_C: col_kernel<L, COL_RESID_C><<<grid, block, 0, s>>>(a); break;
-    case COL_FWD: col_kernel<L, COL_FWD><<<grid, block, 0, s>>>(a); break;
-    case COL_INV: col_kernel<L, COL_INV><<<grid, block, 0, s>>>(a); break;
+    case COL_PASS_NO2DF: return launch_col_pass<L, COL_PASS_MERGE>(a, s);  // same update with N0 = 0
+    case COL_RESID_A: return launch_pdl(col_kernel<L, COL_RESID_A>, grid, block, 0, s, a);
+    case COL_RESID_C: return launch_pdl(col_kernel<L, COL_RESID_C>, grid, block, 0, s, a);
+    case COL_FWD: return launch_pdl(col_kernel<L, COL_FWD>, grid, block, 0, s, a);
+    case COL_INV: return launch_pdl(col_kernel<L, COL_INV>, grid, block, 0, s, a);
     case COL_PASS_MERGE: return launch_col_pass<L, COL_PASS_MERGE>(a, s);
-    case COL_G_FROM_S: col_kernel<L, COL_G_FROM_S><<<grid, block, 0, s>>>(a); break;
-    case COL_UNTILE: col_kernel<L, COL_UNTILE><<<grid, block, 0, s>>>(a); break;
+    case COL_PASS_MERGE_SRC: return launch_col_pass<L, COL_PASS_MERGE_SRC>(a, s);
+    case COL_G_FROM_S: return launch_pdl(col_kernel<L, COL_G_FROM_S>, grid, block, 0, s, a);
+    case COL_UNTILE: return launch_pdl(col_kernel<L, COL_UNTILE>, grid, block, 0, s, a);
+    case COL_FWD_TILED: return launch_pdl(col_kernel<L, COL_FWD_TILED>, grid, block, 0, s, a);
     default: return (int)cudaErrorInvalidValue;
   }
   return (int)cudaGetLastError();

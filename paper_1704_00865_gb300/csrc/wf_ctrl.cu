@@ -286,6 +286,8 @@ constexpr int CTRL_THREADS = 256;
 __global__ void __launch_bounds__(CTRL_THREADS) ctrl_kernel(CtrlArgs a) {
   __shared__ double red[CTRL_THREADS / 32];
   WfState* st = a.st;
+  pdl_trigger();
+  pdl_wait();
   if (a.count_iters && st->done) return;
   double gm2 = 0.0, g2 = 0.0, r2 = 0.0;
   for (int i = threadIdx.x; i < a.nrow; i += blockDim.x) {
@@ -343,8 +345,7 @@ __global__ void __launch_bounds__(CTRL_THREADS) ctrl_kernel(CtrlArgs a) {
 }
 
 int launch_ctrl(const CtrlArgs& a, cudaStream_t s) {
-  ctrl_kernel<<<1, CTRL_THREADS, 0, s>>>(a);
-  return (int)cudaGetLastError();
+  return launch_pdl(ctrl_kernel, dim3(1), dim3(CTRL_THREADS), 0, s, a);
 }
 
 }  // namespace wf

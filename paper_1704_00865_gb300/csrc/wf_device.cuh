@@ -142,6 +142,25 @@ struct StageRadix {
   static constexpr int value = rem >= E ? E : rem;
 };
 
+// Programmatic dependent launch.  A kernel launched with programmatic stream
+// serialisation may start while the previous kernel on the stream is still
+// running; pdl_wait() blocks until that kernel has completed and its writes
+// are visible (a no-op for an ordinary launch), so everything before it may
+// only touch shared memory and tables that no kernel of the iteration
+// writes.  pdl_trigger() lets the next kernel start its own prologue.
+// Every kernel launched this way calls pdl_wait() on every path, so the
+// completion of the last kernel implies that of all before it.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Twiddle read: read-only global path, or a plain load when the table has
+// been staged in shared memory (TWS = true).
+template <bool TWS>
+__device__ __forceinline__ float2 tw_load(const float2* __restrict__ tab, int i) {
+  if constexpr (TWS) return tab[i];
+  else return __ldg(&tab[i]);
+}
+
 // Barrier between the exchange steps of a transform: the whole block, or
 // only the warp when one warp owns the transform (WARP = true).
 template <bool WARP>
@@ -156,7 +175,7 @@ __device__ __forceinline__ void fft_sync() {
 // b + r*(E/R)); outputs go to shared memory at their autosort positions, or,
 // for the last stage, back to the registers in the natural layout.
 // twtab holds exp(-2 pi i k / (L*twstride)), k < L*twstride.
-template <int L, int E, int NS, bool INV, bool WARP>
+template <int L, int E, int NS, bool INV, bool WARP, bool TWS = false>
 struct FFTStages {
   static __device__ __forceinline__ void run(float2 (&v)[E], float2* sb, int t,
                                              const float2* __restrict__ twtab, int twstride) {
@@ -175,11 +194,11 @@ struct FFTStages {
         // twiddles W_{NS R}^{jm r}: exact table values every 4th power,
         // products in between (at most 3 multiplications deep)
         const int step = jm * (L / (NS * R)) * twstride;
-        float2 w1 = tw_dir<INV>(__ldg(&twtab[step]));
+        float2 w1 = tw_dir<INV>(tw_load<TWS>(twtab, step));
         float2 wr = w1;
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-          if ((r & 3) == 0) wr = tw_dir<INV>(__ldg(&twtab[step * r]));
+          if ((r & 3) == 0) wr = tw_dir<INV>(tw_load<TWS>(twtab, step * r));
           u[r] = cmul(u[r], wr);
           wr = cmul(wr, w1);
         }
@@ -199,7 +218,7 @@ struct FFTStages {
 #pragma unroll
       for (int m = 0; m < E; ++m) v[m] = sb[spad(t + m * TPF)];
       fft_sync<WARP>();
-      FFTStages<L, E, NS * R, INV, WARP>::run(v, sb, t, twtab, twstride);
+      FFTStages<L, E, NS * R, INV, WARP, TWS>::run(v, sb, t, twtab, twstride);
     }
   }
 };
@@ -207,10 +226,19 @@ struct FFTStages {
 // Full complex DFT of length L (no scaling).  Every thread of the block (or
 // of the warp, WARP = true) must call it; sb is this transform's own padded
 // shared buffer of SPad<L>::size values.
-template <int L, int E, bool INV, bool WARP = false>
+template <int L, int E, bool INV, bool WARP = false, bool TWS = false>
 __device__ __forceinline__ void fft_block(float2 (&v)[E], float2* sb, int t,
                                           const float2* __restrict__ twtab, int twstride) {
-  FFTStages<L, E, 1, INV, WARP>::run(v, sb, t, twtab, twstride);
+  FFTStages<L, E, 1, INV, WARP, TWS>::run(v, sb, t, twtab, twstride);
+}
+
+// W_N^k (N = 2M) for the k = t + m*(M/E) a thread handles in c2r_pre and
+// r2c_post; loaded once, early, and passed to both.
+template <int M, int E>
+__device__ __forceinline__ void load_rtw(float2 (&wk)[E], int t, const float2* __restrict__ twx) {
+  constexpr int TPF = M / E;
+#pragma unroll
+  for (int m = 0; m < E; ++m) wk[m] = __ldg(&twx[t + m * TPF]);
 }
 
 // ---------------------------------------------------------------- real rows
@@ -221,6 +249,52 @@ __device__ __forceinline__ void fft_block(float2 (&v)[E], float2* sb, int t,
 // Before an inverse complex FFT: X (natural layout in v) -> Z so that
 // IFFT_M(Z) / M gives z.  Here the 1/N scaling of the inverse real DFT is
 // folded in.  twx = exp(-2 pi i k / N).
+template <int M, int E, bool WARP = false>
+__device__ __forceinline__ void c2r_pre_w(float2 (&v)[E], float2* sb, int t, const float2 (&wk)[E]) {
+  constexpr int TPF = M / E;
+  const float s = 0.5f / (float)M;
+#pragma unroll
+  for (int m = 0; m < E; ++m) sb[spad(t + m * TPF)] = v[m];
+  fft_sync<WARP>();
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const int k = t + m * TPF;
+    float2 X = v[m];
+    if (k == 0) {
+      v[m] = make_float2((X.x + X.y) * s, (X.x - X.y) * s);
+    } else {
+      float2 Xm = cconj(sb[spad(M - k)]);
+      float2 Ek = cadd(X, Xm);
+      float2 Ok = cmul(csub(X, Xm), cconj(wk[m]));
+      v[m] = make_float2((Ek.x - Ok.y) * s, (Ek.y + Ok.x) * s);
+    }
+  }
+  fft_sync<WARP>();
+}
+
+template <int M, int E, bool WARP = false>
+__device__ __forceinline__ void r2c_post_w(float2 (&v)[E], float2* sb, int t, const float2 (&wk)[E]) {
+  constexpr int TPF = M / E;
+#pragma unroll
+  for (int m = 0; m < E; ++m) sb[spad(t + m * TPF)] = v[m];
+  fft_sync<WARP>();
+#pragma unroll
+  for (int m = 0; m < E; ++m) {
+    const int k = t + m * TPF;
+    float2 Z = v[m];
+    if (k == 0) {
+      v[m] = make_float2(Z.x + Z.y, Z.x - Z.y);
+    } else {
+      float2 Zm = cconj(sb[spad(M - k)]);
+      float2 Ek = cscale(cadd(Z, Zm), 0.5f);
+      float2 D = cscale(csub(Z, Zm), 0.5f);
+      float2 Ok = make_float2(D.y, -D.x);
+      v[m] = cadd(Ek, cmul(wk[m], Ok));
+    }
+  }
+  fft_sync<WARP>();
+}
+
 template <int M, int E, bool WARP = false>
 __device__ __forceinline__ void c2r_pre(float2 (&v)[E], float2* sb, int t,
                                         const float2* __restrict__ twx) {

@@ -17,6 +17,36 @@ struct WfState;
 // so a column pass reads whole tiles contiguously and a row pass reads
 // 32-byte pieces.  Row-only fields (d_RF, the pixel table) stay row-major.
 constexpr int WF_TW = 4;
+
+// Kernels of the iteration are launched with programmatic stream
+// serialisation: the next kernel's CTAs may start (and prefetch the tables
+// that stay fixed during a solve) while the previous kernel drains; each
+// kernel waits for its predecessor with griddepcontrol.wait before it reads
+// anything the iteration writes.
+#ifndef WF_PDL
+#define WF_PDL 1
+#endif
+// 1: the passes release the next kernel at entry; 0: after their last
+// transform, before the stores
+#ifndef WF_PDL_EARLY
+#define WF_PDL_EARLY 0
+#endif
+template <typename... KArgs, typename... Args>
+inline int launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                      Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = WF_PDL;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, args...);
+  return (int)(e != cudaSuccess ? e : cudaGetLastError());
+}
 __host__ __device__ __forceinline__ size_t tidx(int y, int kx, int ny) {
   return (size_t)(kx / WF_TW) * ny * WF_TW + (size_t)y * WF_TW + (kx % WF_TW);
 }
@@ -43,7 +73,9 @@ enum ColMode : int {
   COL_PASS_MERGE = 6, // joint (s, t_2DF, d_2DF) update given the RF messenger
   COL_G_FROM_S = 7,   // residual of a given s: g = S^-1 s from s in RF
   COL_UNTILE = 8,     // column-tiled RF field -> row-major (exports)
-  COL_NMODES = 9
+  COL_FWD_TILED = 9,  // RF -> 2D Fourier, column-tiled output
+  COL_PASS_MERGE_SRC = 10,  // COL_PASS_MERGE with a source term (defect correction)
+  COL_NMODES = 11
 };
 
 struct RowArgs {
@@ -67,6 +99,8 @@ struct RowArgs {
   float2* out_rf;
   const float2* in_px;        // pixel pairs
   float2* out_px;
+  const float2* src_px;       // source j on masked pixels (pairs) or nullptr
+  float2* gm_out;             // S^-1 s on masked pixels (pairs), 0 elsewhere, or nullptr
 };
 
 struct ColArgs {
@@ -86,6 +120,7 @@ struct ColArgs {
   float2* r_q;
   const float2* in;           // generic transforms
   float2* out;
+  const float2* src;          // 2D-Fourier source j^ (column-tiled) or nullptr
 };
 
 // launchers (return a cudaError_t as int)

@@ -51,6 +51,8 @@ row_kernel(RowArgs a) {
   constexpr int E = Cfg::E, TPF = Cfg::TPF, ROWS = Cfg::ROWS;
   __shared__ float2 sbuf[ROWS][SPad<M>::size];
   __shared__ double red[(Cfg::THREADS + 31) / 32];
+  pdl_trigger();
+  pdl_wait();
 
   const int g = threadIdx.x / TPF;
   const int t = threadIdx.x - g * TPF;
@@ -80,22 +82,27 @@ row_kernel(RowArgs a) {
 #pragma unroll
     for (int m = 0; m < E; ++m) {
       const float4 q = valid ? a.dn[row0 + t + m * TPF] : make_float4(0.f, -1.f, 0.f, -1.f);
-      float gp[2], qp[2];
+      const float2 jm = (valid && a.src_px != nullptr) ? a.src_px[row0 + t + m * TPF] : make_float2(0.f, 0.f);
+      float gp[2], qp[2], go[2];
       const float gv[2] = {v[m].x, v[m].y}, sv[2] = {w[m].x, w[m].y};
-      const float dv[2] = {q.x, q.z}, nv[2] = {q.y, q.w};
+      const float dv[2] = {q.x, q.z}, nv[2] = {q.y, q.w}, jv[2] = {jm.x, jm.y};
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const double gd = (double)gv[h];
         if (valid) g2 += gd * gd;
-        if (nv[h] < 0.f) {  // masked: the residual there is g itself
-          if (valid) gm2 += gd * gd;
+        if (nv[h] < 0.f) {  // masked: the residual there is S^-1 s (minus a source)
+          const double rm = gd - (double)jv[h];
+          if (valid) gm2 += rm * rm;
           gp[h] = 0.f;
           qp[h] = 0.f;
+          go[h] = gv[h];
         } else {             // N_PX g' + s - d with the full pixel variance
           gp[h] = gv[h];
           qp[h] = fmaf(nv[h] + vshift, gv[h], sv[h] - dv[h]);
+          go[h] = 0.f;
         }
       }
+      if (valid && a.gm_out != nullptr) a.gm_out[row0 + t + m * TPF] = make_float2(go[0], go[1]);
       v[m] = make_float2(gp[0], gp[1]);
       w[m] = make_float2(qp[0], qp[1]);
     }
@@ -235,7 +242,6 @@ row_pass_kernel(RowArgs a) {
   float2* s_x = reinterpret_cast<float2*>(smem + SM::x_off);
   float2* s_fft = reinterpret_cast<float2*>(smem + SM::fft_off);
 
-  if (a.check_done && a.st->done) return;  // uniform: set only between launches
   const int g = threadIdx.x / TPF;
   const int t = threadIdx.x - g * TPF;
   const int y0 = blockIdx.x * ROWS;
@@ -250,6 +256,33 @@ row_pass_kernel(RowArgs a) {
     mbar_fence_init();
   }
   fft_sync<W>();
+  if constexpr (WF_PDL_EARLY) pdl_trigger();
+  // before the previous kernel has finished: the pixel table (fixed during a
+  // solve) and the real-transform twiddles
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(&bar[1], (uint32_t)(nval * M * 16));
+    for (int r = 0; r < nval; ++r) bulk_g2s(s_dn + r * M, a.dn + (size_t)(y0 + r) * M, M * 16, &bar[1]);
+  }
+  float2 wk[E];
+  load_rtw<M, E>(wk, t, a.twx);
+  // stripe spectrum a(y)^2 Pst(k) of this thread's modes (fixed during a solve)
+  float pk[RF ? E : 1];
+  float a2y = 1.f, pkn = 0.f;  // pkn: Pst at kx = M, packed with kx = 0
+  if constexpr (RF) {
+    if (a.a2 != nullptr && valid) a2y = __ldg(&a.a2[y]);
+#pragma unroll
+    for (int m = 0; m < E; ++m) pk[m] = __ldg(&a.pst[t + m * TPF]);
+    if (t == 0) pkn = __ldg(&a.pst[M]);
+  }
+  pdl_wait();
+  if (a.check_done && a.st->done) {  // uniform: set only between launches
+    if (!mbar_wait(&bar[1], 0, WF_WAIT_TRIES) && threadIdx.x == 0) atomicOr(&a.st->err, WF_ERR_TIMEOUT);
+    return;
+  }
+  // link covariances of this lambda level (written by the controller)
+  const float T2 = a.st->Tf[2];
+  const float T1 = RF ? a.st->Tf[1] : 0.f;
+  const float off1 = RF ? (float)a.st->off[1] : 0.f;
   if (threadIdx.x == 0) {
     if constexpr (RF) {
       mbar_expect_tx(&bar[0], (uint32_t)(nval * M * 8));
@@ -257,8 +290,6 @@ row_pass_kernel(RowArgs a) {
     } else {
       mbar_expect_tx(&bar[0], 0u);  // nothing on this barrier: completes at once
     }
-    mbar_expect_tx(&bar[1], (uint32_t)(nval * M * 16));
-    for (int r = 0; r < nval; ++r) bulk_g2s(s_dn + r * M, a.dn + (size_t)(y0 + r) * M, M * 16, &bar[1]);
   }
   if constexpr (RF) {
     gather_tiled_rows<M, NT>(s_t1, a.f_t1, y0, nval, a.ny);
@@ -282,10 +313,9 @@ row_pass_kernel(RowArgs a) {
   }
 
   float2 v[E];
-  const float T2 = a.st->Tf[2];
 #pragma unroll
   for (int m = 0; m < E; ++m) v[m] = s_a[g * M + t + m * TPF];
-  c2r_pre<M, E, W>(v, sb, t, a.twx);
+  c2r_pre_w<M, E, W>(v, sb, t, wk);
   fft_block<M, E, true, W>(v, sb, t, a.twx, 2);
   if (__syncthreads_or(!mbar_wait(&bar[1], 0, WF_WAIT_TRIES))) {
     give_up();
@@ -298,7 +328,8 @@ row_pass_kernel(RowArgs a) {
     v[m] = make_float2(tpx_update(q.x, q.y, v[m].x, T2), tpx_update(q.z, q.w, v[m].y, T2));
   }
   fft_block<M, E, false, W>(v, sb, t, a.twx, 2);
-  r2c_post<M, E, W>(v, sb, t, a.twx);
+  r2c_post_w<M, E, W>(v, sb, t, wk);
+  if constexpr (!WF_PDL_EARLY) pdl_trigger();
   if constexpr (RF) {
     cp_async_wait<0>();
     fft_sync<W>();
@@ -310,9 +341,6 @@ row_pass_kernel(RowArgs a) {
     for (int m = 0; m < E; ++m) a.f_y[tidx(y, t + m * TPF, a.ny)] = v[m];
   } else {
     // eqs. (2mess_d0), (2mess_t0) analogues in the stripe basis
-    const float T1 = a.st->Tf[1];
-    const float off1 = (float)a.st->off[1];
-    const float a2y = (a.a2 != nullptr) ? a.a2[y] : 1.f;
 #pragma unroll
     for (int m = 0; m < E; ++m) {
       const int k = t + m * TPF;
@@ -321,13 +349,13 @@ row_pass_kernel(RowArgs a) {
       const float2 t2 = v[m];
       float2 d1, t1;
       if (k == 0) {  // packed (kx = 0, kx = M) real pair
-        const float nr = fmaf(a2y, a.pst[0], off1), ni = fmaf(a2y, a.pst[M], off1);
+        const float nr = fmaf(a2y, pk[0], off1), ni = fmaf(a2y, pkn, off1);
         d1.x = __fdividef(fmaf(nr, t2.x, T2 * t1o.x), nr + T2);
         d1.y = __fdividef(fmaf(ni, t2.y, T2 * t1o.y), ni + T2);
         t1.x = __fdividef(fmaf(T1, d1.x, nr * xo.x), nr + T1);
         t1.y = __fdividef(fmaf(T1, d1.y, ni * xo.y), ni + T1);
       } else {
-        const float nb = fmaf(a2y, __ldg(&a.pst[k]), off1);
+        const float nb = fmaf(a2y, pk[m], off1);
         const float wa = __fdividef(nb, nb + T2);      // weight of t_PX
         d1 = make_float2(fmaf(wa, t2.x - t1o.x, t1o.x), fmaf(wa, t2.y - t1o.y, t1o.y));
         const float wb = __fdividef(nb, nb + T1);      // weight of x
@@ -351,8 +379,7 @@ static int launch_row_pass(const RowArgs& a, cudaStream_t s) {
     configured = true;
   }
   const dim3 grid((a.ny + Cfg::ROWS - 1) / Cfg::ROWS), block(Cfg::THREADS);
-  row_pass_kernel<M, MODE><<<grid, block, bytes, s>>>(a);
-  return (int)cudaGetLastError();
+  return launch_pdl(row_pass_kernel<M, MODE>, grid, block, bytes, s, a);
 }
 
 template <int M>
@@ -362,10 +389,10 @@ static int launch_row_M(int mode, const RowArgs& a, cudaStream_t s) {
   switch (mode) {
     case ROW_PASS_RF: return launch_row_pass<M, ROW_PASS_RF>(a, s);
     case ROW_PASS_NORF: return launch_row_pass<M, ROW_PASS_NORF>(a, s);
-    case ROW_RESID_B: row_kernel<M, ROW_RESID_B><<<grid, block, 0, s>>>(a); break;
-    case ROW_RESID_D: row_kernel<M, ROW_RESID_D><<<grid, block, 0, s>>>(a); break;
-    case ROW_C2R: row_kernel<M, ROW_C2R><<<grid, block, 0, s>>>(a); break;
-    case ROW_R2C: row_kernel<M, ROW_R2C><<<grid, block, 0, s>>>(a); break;
+    case ROW_RESID_B: return launch_pdl(row_kernel<M, ROW_RESID_B>, grid, block, 0, s, a);
+    case ROW_RESID_D: return launch_pdl(row_kernel<M, ROW_RESID_D>, grid, block, 0, s, a);
+    case ROW_C2R: return launch_pdl(row_kernel<M, ROW_C2R>, grid, block, 0, s, a);
+    case ROW_R2C: return launch_pdl(row_kernel<M, ROW_R2C>, grid, block, 0, s, a);
     default: return (int)cudaErrorInvalidValue;
   }
   return (int)cudaGetLastError();

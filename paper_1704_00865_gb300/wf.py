@@ -38,7 +38,8 @@ class wf_params(C.Structure):
     _fields_ = [("theta", C.c_double * 3), ("split_f", C.c_double), ("split_fp", C.c_double),
                 ("split_w", C.c_double), ("tol_u_scale", C.c_double), ("residual_every", C.c_int), ("max_iters", C.c_int),
                 ("check_every", C.c_int), ("merge_2df", C.c_int), ("refine", C.c_int),
-                ("refine_tol_scale", C.c_double), ("reserved", C.c_int * 2)]
+                ("refine_tol_scale", C.c_double), ("refine_max_iters", C.c_int),
+                ("refine_lam1_iters", C.c_int)]
 
 
 class wf_stats(C.Structure):
@@ -145,8 +146,13 @@ def wf_params_default() -> wf_params:
 
 def make_params(theta=None, split_f=None, split_w=None, residual_every=None, max_iters=None,
                 check_every=None, merge_2df=None, tol_u_scale=None, split_fp=None,
-                refine=None, refine_tol_scale=None) -> wf_params:
+                refine=None, refine_tol_scale=None, refine_max_iters=None,
+                refine_lam1_iters=None) -> wf_params:
     p = wf_params_default()
+    if refine_lam1_iters is not None:
+        p.refine_lam1_iters = int(refine_lam1_iters)
+    if refine_max_iters is not None:
+        p.refine_max_iters = int(refine_max_iters)
     if refine_tol_scale is not None:
         p.refine_tol_scale = float(refine_tol_scale)
     if refine is not None:

@@ -1,0 +1,89 @@
+"""CUDA path against the FP64 oracle at the largest sizes the kernels take.
+
+* the 1024 x 1024 three-part masked workload in the launch configuration of
+  the benchmark, and the 4096 x 4096 map with the same noise model: every
+  stored field after a few sweeps, element by element;
+* the longest rows and columns (4096) in both sweep forms, which select
+  the narrowest column-pass staging (one or two columns per CTA);
+* a 4096 x 4096 homogeneous map solved to convergence against the closed
+  form (Sec. 3: every part diagonal in the 2D DFT).
+"""
+
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_util import field, make_plan, oracle_fields, rel
+from paper_1704_00865_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def wf():
+    from paper_1704_00865_gb300 import build, wf
+    build.build()
+    wf.load()
+    O.set_workers(os.cpu_count() or 1)
+    return wf
+
+
+def _sweeps_match(prob, merge, lams, tol=2e-5):
+    sfp = 0.5 if merge else 0.3
+    plan = make_plan(prob, merge_2df=merge, split_f=0.5, split_fp=sfp)
+    P = O.build_parts(prob, merge_2df=bool(merge), split_f=0.5, split_fp=sfp)
+    ch = O.Chain(P)
+    worst = 0.0
+    for lam in lams:
+        plan.iterate(lam, 1)
+        ch.sweep(lam)
+    for fid, ref in oracle_fields(ch).items():
+        e = rel(field(plan, fid), ref)
+        worst = max(worst, e)
+        assert e < tol, (prob.shape, merge, fid, e)
+    plan.close()
+    return worst
+
+
+@pytest.mark.parametrize("merge", [1, 0])
+def test_full_size_1024_sweeps_field_by_field(wf, merge):
+    prob = synth.cfg1_problem(1000, 1024)
+    worst = _sweeps_match(prob, merge, [10.0, 10.0, 10.0, 1.0])
+    print(f"1024^2 merge={merge}: worst field rel L2 {worst:.2e}")
+
+
+@pytest.mark.parametrize("merge", [1, 0])
+def test_4096_map_sweeps_field_by_field(wf, merge):
+    # the 4096 x 4096 map with white + 1/f + stripes noise and the disc mask
+    prob = synth.make_problem(4096, 4096, 3000)
+    worst = _sweeps_match(prob, merge, [10.0, 1.0])
+    print(f"4096^2 merge={merge}: worst field rel L2 {worst:.2e}")
+
+
+@pytest.mark.parametrize("merge", [1, 0])
+@pytest.mark.parametrize("shape", [(4096, 64), (64, 4096), (2048, 128), (128, 2048)])
+def test_longest_rows_and_columns(wf, shape, merge):
+    prob = synth.make_problem(*shape, 41, mask_frac=0.05, stripe_rows_vary=True)
+    _sweeps_match(prob, merge, [50.0, 3.0, 1.0])
+
+
+def test_4096_homogeneous_converges_to_closed_form(wf):
+    from gpu_util import dev
+    import torch
+    # the FP32 floor of ||Delta d_u||/||d_u|| rises with the map size (about
+    # 3e-4 here), so the stop test of the first solve sits above it
+    prob = synth.make_problem(4096, 4096, 3001, homogeneous=True, mask_frac=0.0)
+    sched = wf.make_schedule("fixed", O.cooling_levels(1e3, 10), [100] * 10)
+    plan = wf.Plan(4096, 4096, wf.parts_of(prob),
+                   wf.make_params(refine=1, residual_every=20, max_iters=100000, tol_u_scale=50.0))
+    out = torch.empty(4096, 4096, device="cuda")
+    _, st = plan.solve(dev(prob.d), dev(prob.pixel_var), dev(prob.mask), dev(prob.C), dev(prob.P1f),
+                       dev(prob.Pst), dev(prob.stripe_amp2), sched, 1e-5, out=out)
+    plan.close()
+    s = out.cpu().numpy().astype(np.float64)
+    err = rel(s, O.closed_form(prob))
+    print(f"4096^2 homogeneous: {st['iters']} iterations, rel L2 vs closed form {err:.2e}")
+    assert st["status"] == 0, st
+    assert err < 1e-4
