@@ -36,7 +36,7 @@ struct wf_plan_s {
   float2 *f_d1 = nullptr, *f_t1 = nullptr, *f_x = nullptr, *f_y = nullptr, *f_t0 = nullptr;
   float2 *eig = nullptr, *eig_nyq = nullptr;
   float *pst = nullptr, *a2 = nullptr;
-  float2 *twx = nullptr, *twy = nullptr;
+  float2 *twx = nullptr, *twy = nullptr, *twh = nullptr;  // twh: exp(-2 pi i k/(nx/2))
   float2 *r_g = nullptr, *r_q = nullptr;
   double* part = nullptr;
   WfState* st = nullptr;
@@ -225,6 +225,7 @@ int wf_plan_create(wf_plan_t* out, int ny, int nx, unsigned parts, const wf_para
   AL(P->a2, (size_t)ny);
   AL(P->twx, (size_t)nx);
   AL(P->twy, (size_t)ny);
+  AL(P->twh, (size_t)(nx / 2));
   AL(P->r_g, nh);
   AL(P->r_q, nh);
   AL(P->part, (size_t)3 * P->nrow + 4 * 256 + 64);
@@ -275,9 +276,13 @@ int wf_plan_create(wf_plan_t* out, int ny, int nx, unsigned parts, const wf_para
     const double a = 2.0 * M_PI * (double)k / (double)ny;
     ty[k] = make_float2((float)cos(a), (float)-sin(a));
   }
+  // the half-length row transform's table is every other entry of twx
+  std::vector<float2> th(nx / 2);
+  for (int k = 0; k < nx / 2; ++k) th[k] = tx[2 * k];
   cudaError_t e1 = cudaMemcpy(P->twx, tx.data(), nx * sizeof(float2), cudaMemcpyHostToDevice);
   cudaError_t e2 = cudaMemcpy(P->twy, ty.data(), ny * sizeof(float2), cudaMemcpyHostToDevice);
-  if (e1 != cudaSuccess || e2 != cudaSuccess) {
+  cudaError_t e3 = cudaMemcpy(P->twh, th.data(), nx / 2 * sizeof(float2), cudaMemcpyHostToDevice);
+  if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
     wf_plan_destroy(P);
     return WF_ECUDA;
   }
@@ -301,6 +306,7 @@ static RowArgs row_args(wf_plan_s* P) {
   a.pst = P->pst;
   a.a2 = P->a2;
   a.twx = P->twx;
+  a.twh = P->twh;
   a.st = P->st;
   a.r_g = P->r_g;
   a.r_q = P->r_q;

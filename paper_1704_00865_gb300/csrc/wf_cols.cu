@@ -376,16 +376,6 @@ col_pass_kernel(ColArgs a) {
     for (int m = 0; m < E; ++m) egn[m] = __ldg(&a.eig_nyq[t + m * TPC]);
   }
   pdl_wait();
-  if (a.check_done && a.st->done) {  // uniform: set only between launches
-    if (!mbar_wait(&bar[1], 0, WF_WAIT_TRIES) && threadIdx.x == 0) atomicOr(&a.st->err, WF_ERR_TIMEOUT);
-    cp_async_wait<0>();
-    return;
-  }
-  // link covariances of this lambda level (written by the controller)
-  const float Tl = a.has_rf ? a.st->Tf[1] : a.st->Tf[2];  // link to the RF/PX messenger
-  const float off0 = (float)a.st->off[0];
-  const float T0 = Cfg::T0 ? a.st->Tf[0] : 0.f;
-  const float T0s = Cfg::T0 ? a.st->T0s[a.parity] : 0.f;
   // the messenger tile (and the source tile) on barrier 0
   if (threadIdx.x == 0)
     mbar_expect_tx(&bar[0], Cfg::TILED ? (uint32_t)(Cfg::tile * (Cfg::SRC ? 2 : 1)) : 0u);
@@ -394,14 +384,29 @@ col_pass_kernel(ColArgs a) {
   if constexpr (Cfg::SRC) stage_tiled<L, MODE>(s_t0, a.src, col0, a.ny, &bar[0]);
   if constexpr (Cfg::T0) tile_load_rowmajor<L, W, Cfg::THREADS>(s_t0, a.f_t0, col0, ncols);
   cp_async_commit();
+  // link covariances of this lambda level (written by the controller)
+  const float Tl = a.has_rf ? a.st->Tf[1] : a.st->Tf[2];  // link to the RF/PX messenger
+  const float off0 = (float)a.st->off[0];
+  const float T0 = Cfg::T0 ? a.st->Tf[0] : 0.f;
+  const float T0s = Cfg::T0 ? a.st->T0s[a.parity] : 0.f;
+
+  auto drain = [&]() {
+    const bool ok0 = mbar_wait(&bar[0], 0, WF_WAIT_TRIES);
+    const bool ok1 = mbar_wait(&bar[1], 0, WF_WAIT_TRIES);
+    cp_async_wait<0>();
+    if (!(ok0 && ok1)) atomicOr(&a.st->err, WF_ERR_TIMEOUT);
+  };
+  // uniform: the flag is set only between launches; the copies above are
+  // already in flight, so they land before the block exits
+  if (a.check_done && a.st->done) {
+    drain();
+    return;
+  }
   cp_async_wait<1>();
   const bool ok0 = mbar_wait(&bar[0], 0, WF_WAIT_TRIES);
   const bool ok1 = ok0 && mbar_wait(&bar[1], 0, WF_WAIT_TRIES);
   if (__syncthreads_or(!ok1)) {
-    if (threadIdx.x == 0) atomicOr(&a.st->err, WF_ERR_TIMEOUT);
-    mbar_wait(&bar[0], 0, WF_WAIT_TRIES);
-    mbar_wait(&bar[1], 0, WF_WAIT_TRIES);
-    cp_async_wait<0>();
+    drain();
     return;
   }
 

@@ -90,6 +90,7 @@ struct RowArgs {
   const float* pst;           // [nx/2+1] stripe eigenvalues
   const float* a2;            // [ny] a(y)^2 or nullptr
   const float2* twx;          // exp(-2 pi i k/nx), k < nx
+  const float2* twh;          // exp(-2 pi i k/(nx/2)), k < nx/2 (row pass)
   WfState* st;
   float2* r_g;                // residual scratch (RF)
   float2* r_q;

@@ -204,7 +204,8 @@ struct RowPassSmem {
   static constexpr size_t dn_off = a_off + (size_t)ROWS * M * 8;
   static constexpr size_t t1_off = dn_off + (size_t)ROWS * M * 16;
   static constexpr size_t x_off = t1_off + (RF ? (size_t)ROWS * M * 8 : 0);
-  static constexpr size_t fft_off = x_off + (RF ? (size_t)ROWS * M * 8 : 0);
+  static constexpr size_t tw_off = x_off + (RF ? (size_t)ROWS * M * 8 : 0);  // twh, M values
+  static constexpr size_t fft_off = tw_off + (size_t)M * 8;
   static constexpr size_t bytes = fft_off + (size_t)ROWS * SPad<M>::size * 8;
 };
 
@@ -240,6 +241,7 @@ row_pass_kernel(RowArgs a) {
   float4* s_dn = reinterpret_cast<float4*>(smem + SM::dn_off);
   float2* s_t1 = reinterpret_cast<float2*>(smem + SM::t1_off);
   float2* s_x = reinterpret_cast<float2*>(smem + SM::x_off);
+  float2* s_tw = reinterpret_cast<float2*>(smem + SM::tw_off);
   float2* s_fft = reinterpret_cast<float2*>(smem + SM::fft_off);
 
   const int g = threadIdx.x / TPF;
@@ -258,9 +260,10 @@ row_pass_kernel(RowArgs a) {
   fft_sync<W>();
   if constexpr (WF_PDL_EARLY) pdl_trigger();
   // before the previous kernel has finished: the pixel table (fixed during a
-  // solve) and the real-transform twiddles
+  // solve) and the transform twiddles
   if (threadIdx.x == 0) {
-    mbar_expect_tx(&bar[1], (uint32_t)(nval * M * 16));
+    mbar_expect_tx(&bar[1], (uint32_t)(nval * M * 16 + M * 8));
+    bulk_g2s(s_tw, a.twh, (uint32_t)(M * 8), &bar[1]);
     for (int r = 0; r < nval; ++r) bulk_g2s(s_dn + r * M, a.dn + (size_t)(y0 + r) * M, M * 16, &bar[1]);
   }
   float2 wk[E];
@@ -275,14 +278,7 @@ row_pass_kernel(RowArgs a) {
     if (t == 0) pkn = __ldg(&a.pst[M]);
   }
   pdl_wait();
-  if (a.check_done && a.st->done) {  // uniform: set only between launches
-    if (!mbar_wait(&bar[1], 0, WF_WAIT_TRIES) && threadIdx.x == 0) atomicOr(&a.st->err, WF_ERR_TIMEOUT);
-    return;
-  }
-  // link covariances of this lambda level (written by the controller)
-  const float T2 = a.st->Tf[2];
-  const float T1 = RF ? a.st->Tf[1] : 0.f;
-  const float off1 = RF ? (float)a.st->off[1] : 0.f;
+  // the fields the previous kernels wrote
   if (threadIdx.x == 0) {
     if constexpr (RF) {
       mbar_expect_tx(&bar[0], (uint32_t)(nval * M * 8));
@@ -298,17 +294,27 @@ row_pass_kernel(RowArgs a) {
     gather_tiled_rows<M, NT>(s_a, a.f_x, y0, nval, a.ny);
   }
   cp_async_commit();
+  // link covariances of this lambda level (written by the controller)
+  const float T2 = a.st->Tf[2];
+  const float T1 = RF ? a.st->Tf[1] : 0.f;
+  const float off1 = RF ? (float)a.st->off[1] : 0.f;
 
-  auto give_up = [&]() {
-    if (threadIdx.x == 0) atomicOr(&a.st->err, WF_ERR_TIMEOUT);
-    mbar_wait(&bar[0], 0, WF_WAIT_TRIES);
-    mbar_wait(&bar[1], 0, WF_WAIT_TRIES);
+  auto drain = [&]() {
+    const bool ok0 = mbar_wait(&bar[0], 0, WF_WAIT_TRIES);
+    const bool ok1 = mbar_wait(&bar[1], 0, WF_WAIT_TRIES);
     cp_async_wait<0>();
+    if (!(ok0 && ok1)) atomicOr(&a.st->err, WF_ERR_TIMEOUT);
   };
-  bool ok = mbar_wait(&bar[0], 0, WF_WAIT_TRIES);
+  // uniform: the flag is set only between launches; the copies above are
+  // already in flight, so they land before the block exits
+  if (a.check_done && a.st->done) {
+    drain();
+    return;
+  }
+  bool ok = mbar_wait(&bar[0], 0, WF_WAIT_TRIES) && mbar_wait(&bar[1], 0, WF_WAIT_TRIES);
   if constexpr (!RF) cp_async_wait<0>();
   if (__syncthreads_or(!ok)) {
-    give_up();
+    drain();
     return;
   }
 
@@ -316,18 +322,14 @@ row_pass_kernel(RowArgs a) {
 #pragma unroll
   for (int m = 0; m < E; ++m) v[m] = s_a[g * M + t + m * TPF];
   c2r_pre_w<M, E, W>(v, sb, t, wk);
-  fft_block<M, E, true, W>(v, sb, t, a.twx, 2);
-  if (__syncthreads_or(!mbar_wait(&bar[1], 0, WF_WAIT_TRIES))) {
-    give_up();
-    return;
-  }
+  fft_block<M, E, true, W, true>(v, sb, t, s_tw, 1);
   // eq. (2mess_t1) analogue in pixel space, two pixels per complex value
 #pragma unroll
   for (int m = 0; m < E; ++m) {
     const float4 q = s_dn[g * M + t + m * TPF];
     v[m] = make_float2(tpx_update(q.x, q.y, v[m].x, T2), tpx_update(q.z, q.w, v[m].y, T2));
   }
-  fft_block<M, E, false, W>(v, sb, t, a.twx, 2);
+  fft_block<M, E, false, W, true>(v, sb, t, s_tw, 1);
   r2c_post_w<M, E, W>(v, sb, t, wk);
   if constexpr (!WF_PDL_EARLY) pdl_trigger();
   if constexpr (RF) {
