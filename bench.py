@@ -59,6 +59,10 @@ REFINE_MAX_ITERS = 4000
 REFINE_LAM1_ITERS = 500
 RESIDUAL_EVERY = 50
 CHECK_EVERY = 8
+# a first solve whose ||Delta d_u|| stops falling at lambda = 1 (the FP32
+# floor; 20 checkpoints = 1000 sweeps without a 1% drop) goes on to the
+# correction instead of running to MAX_ITERS
+STALL_CHECKS = 20
 MAX_ITERS = 400000
 SPLIT_F = 0.5           # 1/f white floor carried by the stripe part
 SPLIT_FP = 0.5          # 1/f white floor carried by the white part
@@ -68,12 +72,13 @@ SPLIT_FP = 0.5          # 1/f white floor carried by the white part
 ITERS_PER_SOLVE = 15150
 
 
-def solver_params(wf):
+def solver_params(wf, max_iters=MAX_ITERS):
     """wf_params of the benchmark's solve."""
-    return wf.make_params(residual_every=RESIDUAL_EVERY, max_iters=MAX_ITERS, check_every=CHECK_EVERY,
+    return wf.make_params(residual_every=RESIDUAL_EVERY, max_iters=max_iters, check_every=CHECK_EVERY,
                           merge_2df=1, split_f=SPLIT_F, split_fp=SPLIT_FP, tol_u_scale=TOL_U_SCALE,
                           refine=REFINE, refine_max_iters=REFINE_MAX_ITERS,
-                          refine_lam1_iters=REFINE_LAM1_ITERS, refine_tol_scale=1.0)
+                          refine_lam1_iters=REFINE_LAM1_ITERS, refine_tol_scale=1.0,
+                          stall_checks=STALL_CHECKS)
 
 
 def solver_schedule(wf):
@@ -97,7 +102,8 @@ def workload_config():
                      "literal_residual_target": 1e-5, "rel_error_target": 1e-4},
             "refine": {"solves": REFINE, "sweeps_each": REFINE_MAX_ITERS,
                        "of_which_at_lambda_1": REFINE_LAM1_ITERS},
-            "params": {"merge_2df": 1, "split_f": SPLIT_F, "split_fp": SPLIT_FP, "theta": [0.9, 0.9, 1.0]},
+            "params": {"merge_2df": 1, "split_f": SPLIT_F, "split_fp": SPLIT_FP, "theta": [0.9, 0.9, 1.0],
+                       "stall_checks": STALL_CHECKS},
             "residual_every": RESIDUAL_EVERY,
             "l2": "flushed between steps (512 MiB write), outside the timed events"}
 
@@ -378,6 +384,99 @@ def run_gpu(args):
     return 0
 
 
+# ------------------------------------------------------------- batched form
+BATCH_SIZES = [256, 512, 1024, 2048]   # power-of-two part of the uneven-size mix
+BATCH_MAPS = 32
+BATCH_LANES = 8
+
+
+def batch_problems(n=BATCH_MAPS, seed=2000):
+    """Seeded maps of uneven sizes with the headline noise model at
+    amplitudes scaled by exp(U[-0.5, 0.5])."""
+    from paper_1704_00865_gb300 import synth
+    rng = np.random.default_rng(seed)
+    sizes = [int(rng.choice(BATCH_SIZES)) for _ in range(n)]
+    return [synth.make_problem(m, m, seed + 1 + i, amp_jitter=0.5) for i, m in enumerate(sizes)]
+
+
+def run_batch(args):
+    """Batched solves of uneven maps on concurrent lanes against the same maps
+    solved one after another (the plain per-map form), same solver settings."""
+    import torch
+    from paper_1704_00865_gb300 import build, wf
+    build.build()
+    wf.load()
+    probs = batch_problems()
+    shapes = [p.shape for p in probs]
+    dev = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    inputs = [tuple(dev(a) for a in (p.d, p.pixel_var, p.mask, p.C, p.P1f, p.Pst, p.stripe_amp2)) for p in probs]
+    outs = [torch.empty(*sh, device="cuda") for sh in shapes]
+    sched = solver_schedule(wf)
+    stream = torch.cuda.current_stream()
+    res = {}
+    for name, lanes in (("plain", 1), ("batched", BATCH_LANES)):
+        b = wf.Batch(shapes, params=solver_params(wf, max_iters=60000), lanes=lanes)
+        for _ in range(max(args.warmup, 0)):
+            b.solve(inputs, sched, TOL, outs)
+        torch.cuda.synchronize()
+        l0 = b.launch_count()
+        ms = []
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rc, stats = b.solve(inputs, sched, TOL, outs)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        res[name] = dict(solves_per_s=len(shapes) * args.steps / (sum(ms) / 1e3), ms_per_batch=statistics.mean(ms),
+                         launches=b.launch_count() - l0, status=rc, iters=[s["iters"] for s in stats])
+        b.close()
+    px = sum(a * c for a, c in shapes)
+    line = {"metric": "batched WF solves/sec, uneven map sizes", "value": round(res["batched"]["solves_per_s"], 4),
+            "unit": "solves/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(res["batched"]["ms_per_batch"], 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{len(shapes)} maps, sizes from {BATCH_SIZES} (seeded), headline noise model, "
+                                   f"amplitudes x exp(U[-0.5,0.5]); same solver settings as the headline solve",
+                       "sizes": [a for a, _ in shapes], "pixels": px, "lanes": BATCH_LANES},
+            "plain": {"solves_per_s": round(res["plain"]["solves_per_s"], 4),
+                      "ms_per_batch": round(res["plain"]["ms_per_batch"], 3)},
+            "speedup_vs_plain": round(res["batched"]["solves_per_s"] / res["plain"]["solves_per_s"], 3),
+            "iters_per_map": res["batched"]["iters"], "status": res["batched"]["status"],
+            "gpu_launches": res["batched"]["launches"]}
+    print(json.dumps(line))
+    return 0
+
+
+def run_passes(args):
+    """Per-launch time of the two passes of one sweep (merged three-part
+    chain, lambda = 1) on an n x n map with the headline noise model, timed
+    on the device as graph replays (also the small case ncu captures)."""
+    import torch
+    from paper_1704_00865_gb300 import build, synth, wf
+    build.build()
+    wf.load()
+    n = args.size
+    p = synth.make_problem(n, n, SEED + n)
+    dev = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    plan = wf.Plan(n, n, wf.parts_of(p), wf.make_params(merge_2df=1, split_f=SPLIT_F, split_fp=SPLIT_FP))
+    plan.set_problem(*(dev(a) for a in (p.d, p.pixel_var, p.mask, p.C, p.P1f, p.Pst, p.stripe_amp2)))
+    plan.iterate(1.0, 20)
+    reps = max(20, int(2e8 / (n * n)))
+    us_row, us_col = plan.time_passes(1.0, reps)
+    plan.close()
+    px = n * n
+    peak = float(_peaks()[0]["hbm_gbs"])
+    row_gbs, col_gbs = ROW_BYTES_PER_PX * px / us_row / 1e3, COL_BYTES_PER_PX * px / us_col / 1e3
+    sweep_gbs = (ROW_BYTES_PER_PX + COL_BYTES_PER_PX) * px / (us_row + us_col) / 1e3
+    print(json.dumps({"metric": "row and column pass time", "map": [n, n], "launches_timed": reps,
+                      "us_row": round(us_row, 3), "us_col": round(us_col, 3),
+                      "row_gbs": round(row_gbs, 1), "col_gbs": round(col_gbs, 1), "sweep_gbs": round(sweep_gbs, 1),
+                      "sweep_frac_of_hbm": round(sweep_gbs / peak, 4), "hbm_peak_gbs": peak}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -385,9 +484,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="headline", choices=["headline", "batch", "passes"])
+    ap.add_argument("--size", type=int, default=N, help="map side for --workload passes")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "passes":
+        return run_passes(args)
     return run_gpu(args)
 
 

@@ -66,7 +66,10 @@ enum wf_status {
   WF_ETIMEOUT = 4,    /* a bounded device wait gave up                          */
   WF_ECUDA = 5,       /* a CUDA runtime call failed                             */
   WF_ENOMEM = 6,      /* device allocation failed                               */
-  WF_EUNSUPPORTED = 7 /* size or option this build does not handle             */
+  WF_EUNSUPPORTED = 7, /* size or option this build does not handle           */
+  WF_ESTALL = 8       /* the residual stopped falling above the tolerance (the
+                         FP32 floor, see stall_checks); s_out holds the last
+                         iterate                                               */
 };
 
 /* noise parts present (bit mask); WF_PART_WHITE is required */
@@ -140,6 +143,13 @@ typedef struct {
  *  refine_max_iters iteration cap of each correction solve; 0 (default):
  *                  max_iters.  A correction that reaches a nonzero cap does
  *                  not make wf_solve return WF_ENOCONV.
+ *  stall_checks    at lambda = 1, stop the solve (WF_ESTALL) once this many
+ *                  residual checkpoints in a row bring no 1% drop of
+ *                  ||Delta d_u||^2: an FP32 iteration stalls once its slow
+ *                  links move their fields by less than one unit in the last
+ *                  place.  With refine > 0 a stalled first solve goes on to
+ *                  the corrections, and wf_solve then reports WF_OK when the
+ *                  refined s passes the stop test.  0 (default): never.
  *  refine_lam1_iters with a cap and a fixed schedule, each correction runs
  *                  the schedule's levels (lambda > 1) for at most
  *                  refine_max_iters - refine_lam1_iters sweeps and then
@@ -166,6 +176,8 @@ typedef struct {
   double refine_tol_scale;
   int refine_max_iters;
   int refine_lam1_iters;
+  int stall_checks;
+  int reserved;
 } wf_params;
 
 /* Results of a solve. */
@@ -333,6 +345,65 @@ WF_API int wf_time_passes(wf_plan_t plan, double lam, int n, double* us_row,
  */
 WF_API int wf_fft2_noalloc(int ny, int nx, const float* in, float* out,
                            int inverse, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Batched solves: many independent maps of uneven sizes (the parts and
+ * parameters shared).  Every map gets its own plan; the maps are spread over
+ * `lanes` host worker threads, each driving its maps one after another on
+ * its own CUDA stream, so up to `lanes` solves share the GPU at once (small
+ * maps fill only a few SMs each).  A map's result is the one wf_solve gives
+ * for it alone: same kernels, same order, bit for bit.
+ * ------------------------------------------------------------------------ */
+
+typedef struct wf_batch_s* wf_batch_t;
+
+/* One map of a batch; arrays as for wf_solve (host or device), s_out
+ * receives s. */
+typedef struct {
+  const float* d;
+  const float* pixel_var;
+  const uint8_t* mask;
+  const float* C;
+  const float* P1f;
+  const float* Pst;
+  const float* stripe_amp2;
+  float* s_out;
+} wf_map;
+
+/*
+ * wf_batch_create -- plans for nmaps maps, map i of ny[i] x nx[i] pixels.
+ *   nmaps   1 .. 65536
+ *   ny, nx  host arrays of nmaps sizes, each as for wf_plan_create
+ *   parts   as for wf_plan_create, shared by all maps
+ *   p       parameters (NULL: defaults), shared
+ *   lanes   concurrent solves (host threads and streams), 1 .. 64; maps go
+ *           to lanes largest first, each to the lane with the fewest pixels
+ *   stream  the caller's stream: wf_batch_solve starts after the work
+ *           already on it and the caller's later work waits for the batch
+ * Allocates every plan's workspace up front (about 14 maps of 4 ny nx bytes
+ * per map with refine > 0).  Returns WF_EINVAL / WF_EUNSUPPORTED on bad
+ * arguments before any CUDA call.
+ */
+WF_API int wf_batch_create(wf_batch_t* out, int nmaps, const int* ny, const int* nx, unsigned parts,
+                           const wf_params* p, int lanes, void* stream);
+
+/* Release a batch and its plans (NULL is ignored). */
+WF_API void wf_batch_destroy(wf_batch_t batch);
+
+/*
+ * wf_batch_solve -- wf_solve for every map of the batch.
+ *   maps    host array of nmaps wf_map (map i has the batch's size i)
+ *   sched, tol  as for wf_solve, shared
+ *   stats   host array of nmaps wf_stats, or NULL
+ * Returns WF_OK when every map converged, WF_ENOCONV or WF_ESTALL (that of the
+ * first such map) when some did not (their s_out holds the last iterate), or
+ * the first error of any map.
+ */
+WF_API int wf_batch_solve(wf_batch_t batch, const wf_map* maps, const wf_schedule* sched, double tol,
+                          wf_stats* stats);
+
+/* Kernels launched by all plans of the batch since creation. */
+WF_API long long wf_batch_launch_count(wf_batch_t batch);
 
 #ifdef __cplusplus
 }

@@ -137,6 +137,7 @@ const char* wf_strerror(int s) {
     case WF_EINVAL: return "invalid argument (size, NULL, non-finite or asymmetric input)";
     case WF_ENOTPD: return "a covariance eigenvalue is not positive";
     case WF_ENOCONV: return "no convergence within max_iters";
+    case WF_ESTALL: return "the residual stopped falling above the tolerance";
     case WF_ETIMEOUT: return "a device wait timed out";
     case WF_ECUDA: return "CUDA runtime error";
     case WF_ENOMEM: return "device allocation failed";
@@ -175,8 +176,10 @@ void wf_plan_destroy(wf_plan_t P) {
   delete P;
 }
 
-int wf_plan_create(wf_plan_t* out, int ny, int nx, unsigned parts, const wf_params* p, void* stream) {
-  if (!out) return WF_EINVAL;
+}  // extern "C"
+
+// Host-side validation shared by wf_plan_create and wf_batch_create (no CUDA call).
+int wf::check_plan_args(int ny, int nx, unsigned parts, const wf_params* p) {
   if (!size_supported(nx) || !size_supported(ny)) return WF_EUNSUPPORTED;
   if (!(parts & WF_PART_WHITE) || (parts & ~7u)) return WF_EINVAL;
   wf_params prm;
@@ -192,8 +195,20 @@ int wf_plan_create(wf_plan_t* out, int ny, int nx, unsigned parts, const wf_para
     return WF_EINVAL;
   if (!(prm.tol_u_scale > 0.0) || (prm.merge_2df != 0 && prm.merge_2df != 1)) return WF_EINVAL;
   if (prm.refine < 0 || prm.refine > 8 || !(prm.refine_tol_scale >= 1.0) || prm.refine_max_iters < 0 ||
-      prm.refine_lam1_iters < 0)
+      prm.refine_lam1_iters < 0 || prm.stall_checks < 0)
     return WF_EINVAL;
+  return WF_OK;
+}
+
+extern "C" {
+
+int wf_plan_create(wf_plan_t* out, int ny, int nx, unsigned parts, const wf_params* p, void* stream) {
+  if (!out) return WF_EINVAL;
+  const int chk = check_plan_args(ny, nx, parts, p);
+  if (chk != WF_OK) return chk;
+  wf_params prm;
+  if (p) prm = *p;
+  else wf_params_default(&prm);
 
   wf_plan_s* P = new wf_plan_s();
   P->ny = ny;
@@ -411,6 +426,7 @@ static CtrlArgs ctrl_args(wf_plan_s* P) {
   c.nrow = P->nrow;
   c.R = P->p.residual_every;
   c.max_iters = P->p.max_iters;
+  c.stall = P->p.stall_checks;
   c.lam_sched = P->lam_sched;
   c.it_sched = P->it_sched;
   return c;
@@ -624,7 +640,8 @@ static int wf_run_on(wf_plan_t P, const wf_schedule* sch, double tol, wf_stats* 
   }
   P->it_done = it0 + P->h_st->iter;
   if (P->h_st->err & WF_ERR_TIMEOUT) return WF_ETIMEOUT;
-  int status = P->h_st->status == 3 ? WF_ENOCONV : WF_OK;
+  const int hs = P->h_st->status;
+  int status = hs == 3 ? WF_ENOCONV : (hs == 4 ? WF_ESTALL : WF_OK);
   fill_stats(P, st, status);
   return status;
 }
@@ -721,7 +738,8 @@ int wf_solve(wf_plan_t P, const float* d, const float* pixel_var, const uint8_t*
   if (rc) return rc;
   wf_stats s0{};
   int status = wf_run(P, sched, tol, &s0);
-  if (status != WF_OK && status != WF_ENOCONV) return status;
+  auto finished = [](int r) { return r == WF_OK || r == WF_ENOCONV || r == WF_ESTALL; };
+  if (!finished(status)) return status;
   if (P->p.refine == 0) {
     rc = wf_get_field(P, WF_FIELD_S, s_out);
     if (rc) return rc;
@@ -790,12 +808,12 @@ int wf_solve(wf_plan_t P, const float* d, const float* pixel_var, const uint8_t*
     if (P->p.refine_max_iters > 0) P->p.max_iters = P->p.refine_max_iters;
     int sr_status = wf_run(P, &csched, tol * P->p.refine_tol_scale, &sr);
     P->p.max_iters = main_cap;
-    if (sr_status == WF_OK || sr_status == WF_ENOCONV) rc = wf_get_field(P, WF_FIELD_S, P->s_corr);
+    if (finished(sr_status)) rc = wf_get_field(P, WF_FIELD_S, P->s_corr);
     P->has_src = false;
-    if (sr_status != WF_OK && sr_status != WF_ENOCONV) return sr_status;
+    if (!finished(sr_status)) return sr_status;
     if (rc) return rc;
     // a correction that runs to refine_max_iters has done what was asked
-    if (sr_status == WF_ENOCONV && P->p.refine_max_iters == 0) status = WF_ENOCONV;
+    if (sr_status != WF_OK && P->p.refine_max_iters == 0 && status == WF_OK) status = sr_status;
     tot.iters += sr.iters;
     tot.checkpoints += sr.checkpoints;
     CKI(launch_sub(P->s_acc, P->s_corr, npx, P->stream));
@@ -817,6 +835,11 @@ int wf_solve(wf_plan_t P, const float* d, const float* pixel_var, const uint8_t*
   P->loaded = false;
   tot.rel_rho_u = P->h_st->rel_u;
   tot.rel_rho_m = P->h_st->rel_m;
+  if (tol > 0) {
+    // the refined s is judged by the stop test itself
+    const bool pass = tot.rel_rho_u <= tol * P->p.tol_u_scale && tot.rel_rho_m <= tol;
+    status = pass ? WF_OK : (status == WF_OK ? WF_ENOCONV : status);
+  }
   tot.status = status;
   if (st) *st = tot;
   return status;

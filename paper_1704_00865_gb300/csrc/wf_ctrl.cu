@@ -232,6 +232,8 @@ __global__ void set_lambda_kernel(WfState* st, double lam, int reset) {
     st->level = 0;
     st->in_level = 0;
     st->prev_rho2 = -1.0;
+    st->stall_n = 0;
+    st->stall_ref = -1.0;
   }
 }
 
@@ -318,11 +320,25 @@ __global__ void __launch_bounds__(CTRL_THREADS) ctrl_kernel(CtrlArgs a) {
     st->status = a.tol > 0 ? 3 : 0;  // WF_ENOCONV
     return;
   }
+  // stagnation at lambda = 1: an FP32 iteration stops improving once the
+  // slow links move their fields by less than one unit in the last place
+  if (a.stall > 0 && a.tol > 0 && st->lam == 1.0) {
+    if (st->stall_ref <= 0.0 || r2 < 0.99 * st->stall_ref) {
+      st->stall_ref = r2;
+      st->stall_n = 0;
+    } else if (++st->stall_n >= a.stall) {
+      st->done = 1;
+      st->status = 4;  // WF_ESTALL
+      return;
+    }
+  }
   if (a.mode == 0) {
     if (st->level < a.nlevels - 1 && st->in_level >= a.it_sched[st->level]) {
       st->level += 1;
       st->lam = a.lam_sched[st->level];
       st->in_level = 0;
+      st->stall_ref = -1.0;
+      st->stall_n = 0;
       set_T(st);
     }
   } else if (st->lam > 1.0) {
@@ -336,6 +352,8 @@ __global__ void __launch_bounds__(CTRL_THREADS) ctrl_kernel(CtrlArgs a) {
         st->lam = lam;
         st->in_level = 0;
         st->prev_rho2 = -1.0;
+        st->stall_ref = -1.0;
+        st->stall_n = 0;
         set_T(st);
         return;
       }

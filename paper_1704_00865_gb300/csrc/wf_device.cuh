@@ -49,6 +49,21 @@ __device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2&
   a3 = csub(d02, d13);
 }
 
+// 3-point DFT: with w = exp(-+ 2 pi i / 3) = -1/2 -+ i sqrt(3)/2,
+// X0 = a + b + c, X1 = a + w b + w^2 c, X2 = a + w^2 b + w c, i.e.
+// X1,2 = a - (b + c)/2 -+ i (sqrt(3)/2)(b - c)  (forward: upper sign).
+#define WF_S3 0.86602540378443865f
+template <bool INV>
+__device__ __forceinline__ void dft3(float2& a, float2& b, float2& c) {
+  const float2 s = cadd(b, c), d = csub(b, c);
+  const float2 m = make_float2(fmaf(-0.5f, s.x, a.x), fmaf(-0.5f, s.y, a.y));
+  // -i (sqrt3/2) d (forward) or +i (sqrt3/2) d (inverse)
+  const float2 r = INV ? make_float2(-WF_S3 * d.y, WF_S3 * d.x) : make_float2(WF_S3 * d.y, -WF_S3 * d.x);
+  a = cadd(a, s);
+  b = cadd(m, r);
+  c = csub(m, r);
+}
+
 // cos(pi/4), cos(pi/8), sin(pi/8)
 #define WF_C4 0.70710678118654752f
 #define WF_C8 0.92387953251128674f
@@ -122,7 +137,8 @@ __device__ __forceinline__ void dft16(float2* a) {
 
 template <int R, bool INV>
 __device__ __forceinline__ void dftR(float2* u) {
-  if constexpr (R == 2) dft2<INV>(u[0], u[1]);
+  if constexpr (R == 3) dft3<INV>(u[0], u[1], u[2]);
+  else if constexpr (R == 2) dft2<INV>(u[0], u[1]);
   else if constexpr (R == 4) dft4<INV>(u[0], u[1], u[2], u[3]);
   else if constexpr (R == 8) dft8<INV>(u);
   else if constexpr (R == 16) dft16<INV>(u);
@@ -135,12 +151,20 @@ __device__ __forceinline__ int spad(int i) { return i + (i >> 4); }
 template <int L>
 struct SPad { static constexpr int size = L + L / 16; };
 
-// Radix of the stage that starts with sub-transform length NS.
+// Radix of the stage that starts with sub-transform length NS.  Lengths are
+// 2^k or 3 * 2^k: a factor 3 is taken by the first stage (E then holds a
+// factor 3 too), the rest by powers of two up to the largest one dividing E.
 template <int L, int E, int NS>
 struct StageRadix {
+  static_assert(L % 3 != 0 || E % 3 == 0, "lengths 3*2^k need a factor 3 in E");
+  static constexpr int P2 = E & -E;  // largest power of two dividing E
   static constexpr int rem = L / NS;
-  static constexpr int value = rem >= E ? E : rem;
+  static constexpr int value = (NS == 1 && L % 3 == 0) ? 3 : (rem >= P2 ? P2 : rem);
 };
+
+// (L - k) mod L for 0 <= k < L: the index of the mode -k.
+template <int L>
+__device__ __forceinline__ int neg_mod(int k) { return k == 0 ? 0 : L - k; }
 
 // Programmatic dependent launch.  A kernel launched with programmatic stream
 // serialisation may start while the previous kernel on the stream is still
@@ -186,7 +210,7 @@ struct FFTStages {
 #pragma unroll
     for (int b = 0; b < B; ++b) {
       const int j = t + b * TPF;
-      const int jm = j & (NS - 1);
+      const int jm = j % NS;
       float2 u[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) u[r] = v[b + r * B];
@@ -417,11 +441,13 @@ struct WfState {
   double prev_rho2;   // adaptive rule reference (< 0: none)
   double rho2, gm2, g2, rel_u, rel_m;
   int done;           // 1: stop (converged or out of iterations)
-  int status;         // WF_OK / WF_ENOCONV
+  int status;         // 0 converged, 3 out of iterations, 4 stalled
   int iter;           // iterations completed in this run
   int checkpoints;
   int level, in_level;
-  int pad_[2];
+  int stall_n;        // checkpoints at lambda = 1 without a 1% drop of rho2
+  int pad_;
+  double stall_ref;   // rho2 those checkpoints are measured against (<= 0: none)
 };
 
 enum : unsigned {

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/wf.h"
+
 namespace wf {
 
 struct WfState;
@@ -129,6 +131,8 @@ int launch_row(int mode, const RowArgs& a, cudaStream_t s);
 int launch_col(int mode, const ColArgs& a, cudaStream_t s);
 int row_grid(int nx, int ny);  // CTAs of a row pass (size of partial-sum arrays)
 bool size_supported(int n);
+// argument checks of wf_plan_create (host only; WF_OK or a WF_E* code)
+int check_plan_args(int ny, int nx, unsigned parts, const wf_params* p);
 
 // setup / control kernels
 struct SetupArgs {
@@ -170,6 +174,8 @@ struct CtrlArgs {
   int nlevels;
   double ratio, expo, snap;
   int count_iters;            // add R to iter (0 for a residual-only call)
+  int stall;                  // stop after this many checkpoints at lambda = 1
+                              // without a 1% drop of ||Delta d_u||^2 (0: never)
 };
 int launch_ctrl(const CtrlArgs& a, cudaStream_t s);
 int launch_set_lambda(WfState* st, double lam, int reset, cudaStream_t s);

@@ -8,6 +8,8 @@
 // forward row transform, and the stripe-basis updates (eqs. 2mess_d0 and
 // 2mess_t0 analogues: stripe noise, diagonal in the row-wise DFT) follow the
 // forward transform, so a row is read and written once per iteration.
+#include <mutex>
+
 #include "wf_device.cuh"
 #include "wf_internal.h"
 
@@ -15,7 +17,7 @@ namespace wf {
 
 template <int M>
 struct RowCfg {
-  static constexpr int E = (M >= 2048) ? 16 : 8;
+  static constexpr int E = (M % 3 == 0) ? 12 : ((M >= 2048) ? 16 : 8);
   static constexpr int TPF = M / E;
   static constexpr int ROWS = (256 / TPF) >= 1 ? (256 / TPF) : 1;
   static constexpr int THREADS = ROWS * TPF;
@@ -189,7 +191,7 @@ struct RowPassCfg {
   // 8 values per thread (two warps per 1024-point row) measured fastest at
   // 1024^2; the longest rows take 16 to stay within 1024 threads
   static constexpr int E_DEF = (M >= 2048) ? 16 : 8;
-  static constexpr int E = (WF_ROW_E > 0 && WF_ROW_E <= M / 2) ? WF_ROW_E : E_DEF;
+  static constexpr int E = (M % 3 == 0) ? 12 : (WF_ROW_E > 0 && WF_ROW_E <= M / 2) ? WF_ROW_E : E_DEF;
   static constexpr int TPF = M / E;
   static constexpr int ROWS = (TPF >= 32) ? 1 : 32 / TPF;
   static constexpr int THREADS = ROWS * TPF;
@@ -373,13 +375,13 @@ template <int M, int MODE>
 static int launch_row_pass(const RowArgs& a, cudaStream_t s) {
   using Cfg = RowPassCfg<M>;
   constexpr size_t bytes = RowPassSmem<M, MODE>::bytes;
-  static bool configured = false;  // per instantiation
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(row_pass_kernel<M, MODE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return (int)e;
-    configured = true;
-  }
+  // once per instantiation and process (plans may run on several host threads)
+  static std::once_flag once;
+  static cudaError_t cfg_err = cudaSuccess;
+  std::call_once(once, [] {
+    cfg_err = cudaFuncSetAttribute(row_pass_kernel<M, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  });
+  if (cfg_err != cudaSuccess) return (int)cfg_err;
   const dim3 grid((a.ny + Cfg::ROWS - 1) / Cfg::ROWS), block(Cfg::THREADS);
   return launch_pdl(row_pass_kernel<M, MODE>, grid, block, bytes, s, a);
 }
@@ -407,7 +409,10 @@ int launch_row(int mode, const RowArgs& a, cudaStream_t s) {
     case 64: return launch_row_M<64>(mode, a, s);
     case 128: return launch_row_M<128>(mode, a, s);
     case 256: return launch_row_M<256>(mode, a, s);
+    case 192: return launch_row_M<192>(mode, a, s);
+    case 384: return launch_row_M<384>(mode, a, s);
     case 512: return launch_row_M<512>(mode, a, s);
+    case 768: return launch_row_M<768>(mode, a, s);
     case 1024: return launch_row_M<1024>(mode, a, s);
     case 2048: return launch_row_M<2048>(mode, a, s);
     default: return (int)cudaErrorInvalidValue;
@@ -425,7 +430,10 @@ int row_grid(int nx, int ny) {
     case 64: r = rows_per_cta<64>(); break;
     case 128: r = rows_per_cta<128>(); break;
     case 256: r = rows_per_cta<256>(); break;
+    case 192: r = rows_per_cta<192>(); break;
+    case 384: r = rows_per_cta<384>(); break;
     case 512: r = rows_per_cta<512>(); break;
+    case 768: r = rows_per_cta<768>(); break;
     case 1024: r = rows_per_cta<1024>(); break;
     case 2048: r = rows_per_cta<2048>(); break;
     default: r = 1;
@@ -434,7 +442,8 @@ int row_grid(int nx, int ny) {
 }
 
 bool size_supported(int n) {
-  return n >= 32 && n <= 4096 && (n & (n - 1)) == 0;
+  // powers of two from 32 to 4096, and 384, 768, 1536 (3 * 2^k, one radix-3 stage)
+  return (n >= 32 && n <= 4096 && (n & (n - 1)) == 0) || n == 384 || n == 768 || n == 1536;
 }
 
 }  // namespace wf

@@ -17,7 +17,8 @@ import numpy as np
 
 from . import build as _build
 
-WF_OK, WF_EINVAL, WF_ENOTPD, WF_ENOCONV, WF_ETIMEOUT, WF_ECUDA, WF_ENOMEM, WF_EUNSUPPORTED = range(8)
+WF_OK, WF_EINVAL, WF_ENOTPD, WF_ENOCONV, WF_ETIMEOUT, WF_ECUDA, WF_ENOMEM, WF_EUNSUPPORTED, WF_ESTALL = range(9)
+_FINISHED = (WF_OK, WF_ENOCONV, WF_ESTALL)
 WF_PART_WHITE, WF_PART_1F, WF_PART_STRIPE = 1, 2, 4
 WF_SCHED_FIXED, WF_SCHED_ADAPTIVE = 0, 1
 WF_FIELD_S, WF_FIELD_T_2DF, WF_FIELD_D_2DF, WF_FIELD_T_RF, WF_FIELD_D_RF = range(5)
@@ -25,7 +26,8 @@ WF_FIELD_S, WF_FIELD_T_2DF, WF_FIELD_D_2DF, WF_FIELD_T_RF, WF_FIELD_D_RF = range
 # every symbol include/wf.h declares
 EXPORTS = ["wf_version", "wf_strerror", "wf_params_default", "wf_plan_create", "wf_plan_destroy",
            "wf_set_problem", "wf_run", "wf_iterate", "wf_residual", "wf_get_field", "wf_solve",
-           "wf_fft2", "wf_launch_count", "wf_time_passes", "wf_fft2_noalloc"]
+           "wf_fft2", "wf_launch_count", "wf_time_passes", "wf_fft2_noalloc",
+           "wf_batch_create", "wf_batch_destroy", "wf_batch_solve", "wf_batch_launch_count"]
 
 
 class wf_schedule(C.Structure):
@@ -39,7 +41,7 @@ class wf_params(C.Structure):
                 ("split_w", C.c_double), ("tol_u_scale", C.c_double), ("residual_every", C.c_int), ("max_iters", C.c_int),
                 ("check_every", C.c_int), ("merge_2df", C.c_int), ("refine", C.c_int),
                 ("refine_tol_scale", C.c_double), ("refine_max_iters", C.c_int),
-                ("refine_lam1_iters", C.c_int)]
+                ("refine_lam1_iters", C.c_int), ("stall_checks", C.c_int), ("reserved", C.c_int)]
 
 
 class wf_stats(C.Structure):
@@ -51,6 +53,11 @@ class wf_stats(C.Structure):
         return dict(iters=self.iters, checkpoints=self.checkpoints, lam_final=self.lam_final,
                     rel_rho_u=self.rel_rho_u, rel_rho_m=self.rel_rho_m, tau=list(self.tau),
                     status=self.status, parts=self.parts)
+
+
+class wf_map(C.Structure):
+    _fields_ = [("d", C.c_void_p), ("pixel_var", C.c_void_p), ("mask", C.c_void_p), ("C", C.c_void_p),
+                ("P1f", C.c_void_p), ("Pst", C.c_void_p), ("stripe_amp2", C.c_void_p), ("s_out", C.c_void_p)]
 
 
 class WFError(RuntimeError):
@@ -94,10 +101,18 @@ def load(path: Optional[str] = None):
     L.wf_launch_count.argtypes = [vp]
     L.wf_time_passes.argtypes = [vp, C.c_double, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.wf_fft2_noalloc.argtypes = [C.c_int, C.c_int, vp, vp, C.c_int, vp]
+    L.wf_batch_create.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_uint,
+                                  C.POINTER(wf_params), C.c_int, vp]
+    L.wf_batch_destroy.restype = None
+    L.wf_batch_destroy.argtypes = [vp]
+    L.wf_batch_solve.argtypes = [vp, C.POINTER(wf_map), C.POINTER(wf_schedule), C.c_double, C.POINTER(wf_stats)]
+    L.wf_batch_launch_count.argtypes = [vp]
     for n in EXPORTS:
-        if n not in ("wf_strerror", "wf_params_default", "wf_plan_destroy", "wf_launch_count"):
+        if n not in ("wf_strerror", "wf_params_default", "wf_plan_destroy", "wf_launch_count",
+                     "wf_batch_destroy", "wf_batch_launch_count"):
             getattr(L, n).restype = C.c_int
     L.wf_launch_count.restype = C.c_longlong
+    L.wf_batch_launch_count.restype = C.c_longlong
     _LIB = L
     return L
 
@@ -147,8 +162,10 @@ def wf_params_default() -> wf_params:
 def make_params(theta=None, split_f=None, split_w=None, residual_every=None, max_iters=None,
                 check_every=None, merge_2df=None, tol_u_scale=None, split_fp=None,
                 refine=None, refine_tol_scale=None, refine_max_iters=None,
-                refine_lam1_iters=None) -> wf_params:
+                refine_lam1_iters=None, stall_checks=None) -> wf_params:
     p = wf_params_default()
+    if stall_checks is not None:
+        p.stall_checks = int(stall_checks)
     if refine_lam1_iters is not None:
         p.refine_lam1_iters = int(refine_lam1_iters)
     if refine_max_iters is not None:
@@ -263,7 +280,7 @@ class Plan:
     def run(self, schedule, tol: float):
         st = wf_stats()
         rc = load().wf_run(self.h, C.byref(schedule), float(tol), C.byref(st))
-        if rc not in (WF_OK, WF_ENOCONV):
+        if rc not in _FINISHED:
             _check(rc, "wf_run")
         return st.as_dict()
 
@@ -289,7 +306,7 @@ class Plan:
         po, keep = _ptr(out, np.float32, self.ny * self.nx, writable=True)
         st = wf_stats()
         rc = load().wf_solve(self.h, *ptrs, C.byref(schedule), float(tol), po, C.byref(st))
-        if rc not in (WF_OK, WF_ENOCONV):
+        if rc not in _FINISHED:
             _check(rc, "wf_solve")
         return out, st.as_dict()
 
@@ -321,6 +338,60 @@ def wf_fft2_noalloc(ny: int, nx: int, x, out, inverse: bool = False, stream=None
     _check(load().wf_fft2_noalloc(int(ny), int(nx), pi, po, int(bool(inverse)),
                                   stream if stream is not None else _current_stream()), "wf_fft2_noalloc")
     return out
+
+
+class Batch:
+    """Plans for many independent maps of uneven sizes solved together
+    (see wf_batch_create / wf_batch_solve in include/wf.h)."""
+
+    def __init__(self, shapes, parts=WF_PART_WHITE | WF_PART_1F | WF_PART_STRIPE,
+                 params: Optional[wf_params] = None, lanes: int = 8, stream=None):
+        self.shapes = [(int(a), int(b)) for a, b in shapes]
+        n = len(self.shapes)
+        ny = (C.c_int * max(n, 1))(*[a for a, _ in self.shapes])
+        nx = (C.c_int * max(n, 1))(*[b for _, b in self.shapes])
+        self.params = params if params is not None else wf_params_default()
+        self.h = C.c_void_p()
+        _check(load().wf_batch_create(C.byref(self.h), n, ny, nx, int(parts), C.byref(self.params), int(lanes),
+                                      stream if stream is not None else _current_stream()), "wf_batch_create")
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            load().wf_batch_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, problems, schedule, tol, outs):
+        """problems: sequence of (d, pixel_var, mask, C, P1f, Pst, stripe_amp2)
+        in the batch's map order; outs: one output per map.  Returns (status,
+        list of stats dicts)."""
+        n = len(self.shapes)
+        if len(problems) != n or len(outs) != n:
+            raise ValueError("one problem and one output per map")
+        maps = (wf_map * n)()
+        keep = []
+        for i, ((ny, nx), pr, out) in enumerate(zip(self.shapes, problems, outs)):
+            d, pv, mask, Cs, P1f, Pst, amp2 = pr
+            nspec = ny * (nx // 2 + 1)
+            ptrs = [_ptr(d, np.float32, ny * nx), _ptr(pv, np.float32, ny * nx), _ptr(mask, np.uint8, ny * nx),
+                    _ptr(Cs, np.float32, nspec), _ptr(P1f, np.float32, nspec), _ptr(Pst, np.float32, nx // 2 + 1),
+                    _ptr(amp2, np.float32, ny), _ptr(out, np.float32, ny * nx, writable=True)]
+            keep.extend(k for _, k in ptrs)
+            for f, (pp, _) in zip(("d", "pixel_var", "mask", "C", "P1f", "Pst", "stripe_amp2", "s_out"), ptrs):
+                setattr(maps[i], f, pp)
+        stats = (wf_stats * n)()
+        rc = load().wf_batch_solve(self.h, maps, C.byref(schedule), float(tol), stats)
+        if rc not in _FINISHED:
+            _check(rc, "wf_batch_solve")
+        return rc, [s.as_dict() for s in stats]
+
+    def launch_count(self) -> int:
+        return int(load().wf_batch_launch_count(self.h))
 
 
 def parts_of(prob) -> int:

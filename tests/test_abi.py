@@ -68,7 +68,8 @@ def test_plan_create_rejects_bad_arguments_before_any_cuda_call(lib, ny, nx, par
 def test_plan_create_rejects_bad_params(lib):
     from paper_1704_00865_gb300 import wf
     for kw in (dict(theta=(0.9, 1.5, 1.0)), dict(split_f=0.5, split_fp=0.5, merge_2df=0), dict(split_f=1.01, split_fp=0.0), dict(split_f=0.6, split_fp=0.6),
-               dict(residual_every=0), dict(tol_u_scale=0.0), dict(refine=-1), dict(refine=9)):
+               dict(residual_every=0), dict(tol_u_scale=0.0), dict(refine=-1), dict(refine=9),
+               dict(refine_max_iters=-1), dict(refine_lam1_iters=-1), dict(stall_checks=-1)):
         p = wf.make_params(**kw)
         h = C.c_void_p()
         assert lib.wf_plan_create(C.byref(h), 64, 64, 7, C.byref(p), None) == wf.WF_EINVAL
@@ -88,5 +89,35 @@ def test_schedule_struct_layout_matches_header(lib):
     from paper_1704_00865_gb300 import wf
     # int, ptr, ptr, int, 4 doubles on LP64
     assert C.sizeof(wf.wf_schedule) == 4 + 4 + 8 + 8 + 4 + 4 + 32
-    assert C.sizeof(wf.wf_params) == 24 + 24 + 8 + 16 + 8 + 8 + 8
+    assert C.sizeof(wf.wf_params) == 24 + 24 + 8 + 16 + 8 + 8 + 8 + 8
     assert C.sizeof(wf.wf_stats) == 8 + 8 * 3 + 24 + 8
+
+
+@pytest.mark.parametrize("sizes,lanes,parts,code", [
+    ([], 4, 7, 1),                           # no maps
+    ([(64, 64)], 0, 7, 1),                   # no lanes
+    ([(64, 64)], 65, 7, 1),                  # too many lanes
+    ([(64, 64), (64, 1000)], 2, 7, 7),       # one unsupported size
+    ([(64, 64), (128, 32)], 2, 6, 1),        # white part missing
+])
+def test_batch_create_rejects_bad_arguments_before_any_cuda_call(lib, sizes, lanes, parts, code):
+    from paper_1704_00865_gb300 import wf
+    n = len(sizes)
+    ny = (C.c_int * max(n, 1))(*[a for a, _ in sizes])
+    nx = (C.c_int * max(n, 1))(*[b for _, b in sizes])
+    h = C.c_void_p()
+    p = wf.wf_params_default()
+    assert lib.wf_batch_create(C.byref(h), n, ny, nx, parts, C.byref(p), lanes, None) == code
+    assert h.value is None
+    bad = wf.make_params(refine=9)
+    if n:
+        assert lib.wf_batch_create(C.byref(h), n, ny, nx, 7, C.byref(bad), 1, None) in (wf.WF_EINVAL, code)
+
+
+def test_batch_solve_rejects_null_handles(lib):
+    from paper_1704_00865_gb300 import wf
+    s = wf.make_schedule("fixed", [10.0], [10])
+    assert lib.wf_batch_solve(None, None, C.byref(s), 1e-5, None) == wf.WF_EINVAL
+    assert lib.wf_batch_launch_count(None) == -1
+    lib.wf_batch_destroy(None)
+    assert C.sizeof(wf.wf_map) == 8 * 8

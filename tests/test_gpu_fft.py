@@ -10,7 +10,9 @@ from gpu_util import pack_spectrum, rel, unpack_rows, unpack_spectrum
 pytestmark = pytest.mark.gpu
 
 SIZES = [(32, 32), (32, 64), (64, 32), (128, 256), (256, 128), (512, 512), (1024, 1024),
-         (2048, 64), (64, 4096), (4096, 32)]
+         (2048, 64), (64, 4096), (4096, 32),
+         # lengths 3 * 2^k (a radix-3 stage in both directions)
+         (384, 384), (768, 384), (384, 768), (1536, 64), (64, 1536), (1536, 1536), (384, 32), (32, 768)]
 
 
 @pytest.fixture(scope="module")
@@ -32,6 +34,16 @@ def test_forward_2d_matches_brute_force_dft(wf):
     X = unpack_spectrum(p.fft2(x), ny, nx)
     ref = O.brute_dft(O.brute_dft(x.astype(np.float64), axis=0), axis=1)[:, : nx // 2 + 1]
     assert rel(X, ref) < 2e-6
+
+
+@pytest.mark.parametrize("ny,nx", [(384, 32), (32, 768)])
+def test_radix3_lengths_match_brute_force_dft(wf, ny, nx):
+    x = np.random.default_rng(ny + nx).standard_normal((ny, nx)).astype(np.float32)
+    p = _plan(wf, ny, nx)
+    X = unpack_spectrum(p.fft2(x), ny, nx)
+    ref = O.brute_dft(O.brute_dft(x.astype(np.float64), axis=0), axis=1)[:, : nx // 2 + 1]
+    assert rel(X, ref) < 2e-6
+    p.close()
 
 
 @pytest.mark.parametrize("ny,nx", SIZES)

@@ -63,7 +63,9 @@ def test_4096_map_sweeps_field_by_field(wf, merge):
 
 
 @pytest.mark.parametrize("merge", [1, 0])
-@pytest.mark.parametrize("shape", [(4096, 64), (64, 4096), (2048, 128), (128, 2048)])
+@pytest.mark.parametrize("shape", [(4096, 64), (64, 4096), (2048, 128), (128, 2048),
+                                   # 3 * 2^k: radix-3 stages in the row and column passes
+                                   (384, 256), (256, 384), (768, 128), (128, 768), (1536, 64), (64, 1536)])
 def test_longest_rows_and_columns(wf, shape, merge):
     prob = synth.make_problem(*shape, 41, mask_frac=0.05, stripe_rows_vary=True)
     _sweeps_match(prob, merge, [50.0, 3.0, 1.0])
@@ -85,5 +87,23 @@ def test_4096_homogeneous_converges_to_closed_form(wf):
     s = out.cpu().numpy().astype(np.float64)
     err = rel(s, O.closed_form(prob))
     print(f"4096^2 homogeneous: {st['iters']} iterations, rel L2 vs closed form {err:.2e}")
+    assert st["status"] == 0, st
+    assert err < 1e-4
+
+
+@pytest.mark.parametrize("n", [384, 768, 1536])
+def test_radix3_sizes_converge_to_closed_form(wf, n):
+    from gpu_util import dev
+    import torch
+    prob = synth.make_problem(n, n, 3100 + n, homogeneous=True, mask_frac=0.0)
+    sched = wf.make_schedule("fixed", O.cooling_levels(1e3, 10), [100] * 10)
+    plan = wf.Plan(n, n, wf.parts_of(prob),
+                   wf.make_params(refine=1, residual_every=20, max_iters=100000, tol_u_scale=50.0))
+    out = torch.empty(n, n, device="cuda")
+    _, st = plan.solve(dev(prob.d), dev(prob.pixel_var), dev(prob.mask), dev(prob.C), dev(prob.P1f),
+                       dev(prob.Pst), dev(prob.stripe_amp2), sched, 1e-5, out=out)
+    plan.close()
+    err = rel(out.cpu().numpy().astype(np.float64), O.closed_form(prob))
+    print(f"{n}^2 homogeneous: {st['iters']} iterations, rel L2 vs closed form {err:.2e}")
     assert st["status"] == 0, st
     assert err < 1e-4

@@ -220,3 +220,42 @@ def test_defect_correction_goes_far_below_the_fp32_floor(wf, kw):
     err = rel(s, O.dense_wf(prob))
     print(f"refine=2 {kw}: rel L2 vs dense {err:.2e}")
     assert err < 2e-6
+
+
+def test_stall_detector_stops_at_the_fp32_floor(wf):
+    # a tolerance no FP32 iteration can meet: without the detector the run
+    # goes to max_iters; with it, it ends once ||Delta d_u|| stops falling
+    prob = synth.make_problem(64, 128, 51, mask_frac=0.05, k_knee=4.0, k_knee_x=4.0)
+    sched = wf.make_schedule("fixed", O.cooling_levels(1e2, 5), [20] * 5)
+    plan = make_plan(prob, residual_every=10, max_iters=200000, stall_checks=5)
+    st = plan.run(sched, 1e-12)
+    plan.close()
+    assert st["status"] == wf.WF_ESTALL, st
+    assert st["lam_final"] == 1.0 and st["iters"] < 200000
+    # the stalled iterate is the converged one up to the floor
+    assert rel(field_of_run(wf, prob, st["iters"], sched), O.dense_wf(prob)) < 1e-3
+
+
+def field_of_run(wf, prob, iters, sched):
+    plan = make_plan(prob, residual_every=10, max_iters=iters)
+    plan.run(sched, 0.0)
+    s = field(plan, wf.WF_FIELD_S)
+    plan.close()
+    return s
+
+
+def test_refined_solve_after_a_stall_passes_the_stop_test(wf):
+    import torch
+    prob = synth.make_problem(64, 128, 52, mask_frac=0.05, k_knee=4.0, k_knee_x=4.0)
+    sched = wf.make_schedule("fixed", O.cooling_levels(1e2, 5), [20] * 5)
+    # tol_u below the first solve's floor: it stalls, the correction gets there
+    plan = wf.Plan(64, 128, wf.parts_of(prob),
+                   wf.make_params(refine=1, residual_every=10, max_iters=200000, stall_checks=5, tol_u_scale=1.0))
+    out = torch.empty(64, 128, device="cuda")
+    _, st = plan.solve(dev(prob.d), dev(prob.pixel_var), dev(prob.mask), dev(prob.C), dev(prob.P1f),
+                       dev(prob.Pst), dev(prob.stripe_amp2), sched, 3e-6, out=out)
+    plan.close()
+    # the refined s is judged by the stop test itself
+    passes = st["rel_rho_u"] <= 3e-6 and st["rel_rho_m"] <= 3e-6
+    assert (st["status"] == wf.WF_OK) == passes, st
+    assert rel(out.cpu().numpy().astype(np.float64), O.dense_wf(prob)) < 1e-4
