@@ -23,7 +23,7 @@ struct ColPassCfg {
   static constexpr bool T0 = (MODE == COL_PASS_2DF);
   static constexpr bool SRC = (MODE == COL_PASS_MERGE_SRC);
   static constexpr bool EXTRA = T0 || SRC;  // a third staged tile
-  static constexpr int E = (L % 3 == 0) ? 12
+  static constexpr int E = (L % 3 == 0) ? ((L >= 1536) ? 24 : 12)
                            : (WF_COL_E > 0 && WF_COL_E <= L / 2) ? WF_COL_E : ((L >= 512) ? 16 : 8);
   static constexpr int TPC = L / E;
   static constexpr int W_MIN = (TPC >= 32) ? 1 : 32 / TPC;  // at least one warp

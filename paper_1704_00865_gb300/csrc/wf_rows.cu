@@ -189,8 +189,8 @@ row_kernel(RowArgs a) {
 template <int M>
 struct RowPassCfg {
   // 8 values per thread (two warps per 1024-point row) measured fastest at
-  // 1024^2; the longest rows take 16 to stay within 1024 threads
-  static constexpr int E_DEF = (M >= 2048) ? 16 : 8;
+  // 1024^2; the longest rows (2048 complex) then get 8 warps
+  static constexpr int E_DEF = 8;
   static constexpr int E = (M % 3 == 0) ? 12 : (WF_ROW_E > 0 && WF_ROW_E <= M / 2) ? WF_ROW_E : E_DEF;
   static constexpr int TPF = M / E;
   static constexpr int ROWS = (TPF >= 32) ? 1 : 32 / TPF;
@@ -207,8 +207,12 @@ struct RowPassSmem {
   static constexpr size_t t1_off = dn_off + (size_t)ROWS * M * 16;
   static constexpr size_t x_off = t1_off + (RF ? (size_t)ROWS * M * 8 : 0);
   static constexpr size_t tw_off = x_off + (RF ? (size_t)ROWS * M * 8 : 0);  // twh, M values
-  static constexpr size_t fft_off = tw_off + (size_t)M * 8;
-  static constexpr size_t bytes = fft_off + (size_t)ROWS * SPad<M>::size * 8;
+  static constexpr size_t fft_bytes = (size_t)ROWS * SPad<M>::size * 8;
+  // the transform twiddles are staged too unless that would leave room for
+  // only one CTA per SM (the longest rows)
+  static constexpr bool TWS = tw_off + (size_t)M * 8 + fft_bytes <= 110 * 1024;
+  static constexpr size_t fft_off = tw_off + (TWS ? (size_t)M * 8 : 0);
+  static constexpr size_t bytes = fft_off + fft_bytes;
 };
 
 // Gather rows y0 .. y0+nrows-1 of a column-tiled RF field into row-major
@@ -264,8 +268,8 @@ row_pass_kernel(RowArgs a) {
   // before the previous kernel has finished: the pixel table (fixed during a
   // solve) and the transform twiddles
   if (threadIdx.x == 0) {
-    mbar_expect_tx(&bar[1], (uint32_t)(nval * M * 16 + M * 8));
-    bulk_g2s(s_tw, a.twh, (uint32_t)(M * 8), &bar[1]);
+    mbar_expect_tx(&bar[1], (uint32_t)(nval * M * 16 + (SM::TWS ? M * 8 : 0)));
+    if constexpr (SM::TWS) bulk_g2s(s_tw, a.twh, (uint32_t)(M * 8), &bar[1]);
     for (int r = 0; r < nval; ++r) bulk_g2s(s_dn + r * M, a.dn + (size_t)(y0 + r) * M, M * 16, &bar[1]);
   }
   float2 wk[E];
@@ -324,14 +328,14 @@ row_pass_kernel(RowArgs a) {
 #pragma unroll
   for (int m = 0; m < E; ++m) v[m] = s_a[g * M + t + m * TPF];
   c2r_pre_w<M, E, W>(v, sb, t, wk);
-  fft_block<M, E, true, W, true>(v, sb, t, s_tw, 1);
+  fft_block<M, E, true, W, SM::TWS>(v, sb, t, SM::TWS ? s_tw : a.twh, 1);
   // eq. (2mess_t1) analogue in pixel space, two pixels per complex value
 #pragma unroll
   for (int m = 0; m < E; ++m) {
     const float4 q = s_dn[g * M + t + m * TPF];
     v[m] = make_float2(tpx_update(q.x, q.y, v[m].x, T2), tpx_update(q.z, q.w, v[m].y, T2));
   }
-  fft_block<M, E, false, W, true>(v, sb, t, s_tw, 1);
+  fft_block<M, E, false, W, SM::TWS>(v, sb, t, SM::TWS ? s_tw : a.twh, 1);
   r2c_post_w<M, E, W>(v, sb, t, wk);
   if constexpr (!WF_PDL_EARLY) pdl_trigger();
   if constexpr (RF) {
