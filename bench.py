@@ -117,24 +117,30 @@ def problem():
     return synth.cfg1_problem(SEED, N)
 
 
-def _src_sha():
+# the sources each timed kernel is built from
+KERNEL_SOURCES = {"row_pass": ["wf_rows.cu", "wf_device.cuh"],
+                  "col_pass": ["wf_colpass.cu", "wf_cols_common.cuh", "wf_device.cuh"]}
+
+
+def kernel_sha(kernel):
     h = hashlib.sha256()
     cdir = os.path.join(ROOT, "paper_1704_00865_gb300", "csrc")
-    for f in sorted(os.listdir(cdir)):
+    for f in KERNEL_SOURCES[kernel]:
         h.update(open(os.path.join(cdir, f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def _traffic(kernel):
-    """ncu DRAM bytes per launch for `kernel`, if the committed capture was
-    taken on the current kernel sources; else None."""
+    """ncu DRAM bytes (read + write) per launch of `kernel` at the benchmark
+    size, if the committed capture was taken on the current kernel sources;
+    else None."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         d = json.load(open(p))
     except Exception:
         return None
     e = d.get(kernel)
-    if not e or e.get("source_sha") != _src_sha():
+    if not e or e.get("source_sha") != kernel_sha(kernel):
         return None
     return e.get("dram_bytes_per_launch")
 

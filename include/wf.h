@@ -405,6 +405,80 @@ WF_API int wf_batch_solve(wf_batch_t batch, const wf_map* maps, const wf_schedul
 /* Kernels launched by all plans of the batch since creation. */
 WF_API long long wf_batch_launch_count(wf_batch_t batch);
 
+/* ------------------------------------------------------------------------
+ * Learned warm start.  The paper has no network: this is an extension that
+ * predicts s with a Fourier neural operator (FNO) and starts the messenger
+ * iteration from it; the iteration stays the judge of the result.
+ *
+ * Network for input x [B, 2, n, n] (see wf_fno_features):
+ *   h_0 = P x + p;  h_{l+1} = act(W_l h_l + w_l + K_l h_l), l < layers
+ *   (act = GELU, identity after the last layer);  y = Q h_layers + q.
+ * K_l: truncated real 2D DFT of every channel on k_x in [0, mx), k_y in
+ * [0, my) U [n - my, n), one complex width x width matrix per mode, and the
+ * truncated inverse (1/n^2, real part).  Parameters are one FP32 vector in
+ * the order P [width][2], p [width], per layer W_l [width][width], w_l
+ * [width], R_l [width_in][width_out][2 my][mx] as (re, im) pairs, then
+ * Q [1][width], q [1].  Matrices are used in FP16 with FP32 accumulation.
+ * ------------------------------------------------------------------------ */
+
+typedef struct wf_fno_s* wf_fno_t;
+
+/*
+ * wf_fno_create -- a network and its training state for n x n maps and up to
+ * `batch` maps per call.
+ *   n        power of two in [16, 1024];  batch 1 .. 64
+ *   width    even, 2 .. 64;  mx 1 .. min(32, n/2);  my 1 .. min(32, n/2)
+ *   layers   1 .. 8
+ *   params   initial parameters (host or device, FP32, in the order above)
+ *   stream   cudaStream_t for every later call on this network
+ * Adam moments start at zero.
+ */
+WF_API int wf_fno_create(wf_fno_t* out, int n, int batch, int width, int mx, int my, int layers,
+                         const float* params, void* stream);
+WF_API void wf_fno_destroy(wf_fno_t fno);
+
+/* Number of parameters (floats), or -1 for NULL. */
+WF_API long long wf_fno_num_params(wf_fno_t fno);
+
+/* y [nb, n, n] = network(x [nb, 2, n, n]); device arrays; nb <= batch. */
+WF_API int wf_fno_forward(wf_fno_t fno, const float* x, float* y, int nb);
+
+/*
+ * wf_fno_gradient -- loss = mean_b ||y_b - t_b||^2 / ||t_b||^2 over nb maps,
+ * and its gradient with respect to the parameters (as the forward pass uses
+ * them, FP16-rounded matrices) into grad (host or device, num_params floats;
+ * NULL to skip).  x, t device arrays.  Nothing is updated.
+ */
+WF_API int wf_fno_gradient(wf_fno_t fno, const float* x, const float* t, int nb, float* grad, double* loss);
+
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) on the FP32 parameters. */
+WF_API int wf_fno_train_step(wf_fno_t fno, const float* x, const float* t, int nb, double lr, double* loss);
+
+/* Copy the parameters out (host or device): rounded = 0 the FP32 master
+ * values, 1 the values the forward pass uses (FP16-rounded matrices). */
+WF_API int wf_fno_get_params(wf_fno_t fno, float* out, int rounded);
+
+/*
+ * wf_fno_features -- network input of one map: x[0] = d / sigma (0 where
+ * masked), x[1] = log(sigma^2 / pixel_var) (log 1e-6 where masked), with
+ * sigma^2 the mean pixel variance over unmasked pixels, written to
+ * sigma_out (device float).  All pointers device; launched on `stream`.
+ */
+WF_API int wf_fno_features(int ny, int nx, const float* d, const float* pixel_var, const uint8_t* mask,
+                           float* x_out, float* sigma_out, void* stream);
+
+/*
+ * wf_solve_warm -- wf_solve started from an estimate s_init of s (host or
+ * device [ny][nx]) instead of zero: the messenger fields are set to s_init
+ * in their own bases (t_RF = d_RF = s_init row-transformed; the signal-side
+ * field d_2DF = (C + N_0)/C s_init, so that the implicit s equals s_init)
+ * before the schedule runs.  Everything else as wf_solve.
+ */
+WF_API int wf_solve_warm(wf_plan_t plan, const float* d, const float* pixel_var, const uint8_t* mask,
+                         const float* C, const float* P1f, const float* Pst, const float* stripe_amp2,
+                         const float* s_init, const wf_schedule* sched, double tol, float* s_out,
+                         wf_stats* stats);
+
 #ifdef __cplusplus
 }
 #endif

@@ -7,3 +7,4 @@ the CUDA path; both take their inputs from ``paper_1704_00865_gb300.synth``.
 """
 
 from .wf_oracle import *  # noqa: F401,F403
+from . import fno_oracle  # noqa: F401

@@ -730,12 +730,38 @@ int wf_get_field(wf_plan_t P, int field, float* out) {
   return WF_OK;
 }
 
-int wf_solve(wf_plan_t P, const float* d, const float* pixel_var, const uint8_t* mask, const float* C,
-             const float* P1f, const float* Pst, const float* stripe_amp2, const wf_schedule* sched,
-             double tol, float* s_out, wf_stats* st) {
-  if (!s_out) return WF_EINVAL;
+}  // extern "C"
+
+// Messenger fields from an estimate of s: the data-side messengers (t_RF and
+// d_RF, or t_PX without stripes) take s itself in their basis, and the
+// signal-side field the value whose implicit s is s_init.
+static int warm_init(wf_plan_s* P, const float* s_init) {
+  if (P->has_f && !P->merge) return WF_EUNSUPPORTED;  // t_2DF would need its own T_0 history
+  const size_t npx = (size_t)P->ny * P->nx;
+  const float* ds = nullptr;
+  int rc = to_device(P, s_init, P->stg_io, npx, &ds);
+  if (rc) return rc;
+  RowArgs ra = row_args(P);
+  ra.in_px = (const float2*)ds;
+  ra.out_rf = P->r_q;
+  CKI(launch_row(ROW_R2C, ra, P->stream));
+  if (P->f_d1) CK(cudaMemcpyAsync(P->f_d1, P->r_q, npx / 2 * sizeof(float2), cudaMemcpyDeviceToDevice, P->stream));
+  ColArgs ca = col_args(P, 0);
+  ca.in = P->r_q;
+  ca.out = P->f_x;
+  ca.warm_copy = P->has_rf ? P->f_t1 : P->f_y;
+  CKI(launch_col(COL_WARM, ca, P->stream));
+  P->launches += 2;
+  return WF_OK;
+}
+
+static int solve_impl(wf_plan_t P, const float* d, const float* pixel_var, const uint8_t* mask, const float* C,
+                      const float* P1f, const float* Pst, const float* stripe_amp2, const float* s_init,
+                      const wf_schedule* sched, double tol, float* s_out, wf_stats* st) {
+  if (!P || !s_out || !sched) return WF_EINVAL;
   int rc = wf_set_problem(P, d, pixel_var, mask, C, P1f, Pst, stripe_amp2);
   if (rc) return rc;
+  if (s_init && (rc = warm_init(P, s_init))) return rc;
   wf_stats s0{};
   int status = wf_run(P, sched, tol, &s0);
   auto finished = [](int r) { return r == WF_OK || r == WF_ENOCONV || r == WF_ESTALL; };
@@ -843,6 +869,21 @@ int wf_solve(wf_plan_t P, const float* d, const float* pixel_var, const uint8_t*
   tot.status = status;
   if (st) *st = tot;
   return status;
+}
+
+extern "C" {
+
+int wf_solve(wf_plan_t P, const float* d, const float* pixel_var, const uint8_t* mask, const float* C,
+             const float* P1f, const float* Pst, const float* stripe_amp2, const wf_schedule* sched,
+             double tol, float* s_out, wf_stats* st) {
+  return solve_impl(P, d, pixel_var, mask, C, P1f, Pst, stripe_amp2, nullptr, sched, tol, s_out, st);
+}
+
+int wf_solve_warm(wf_plan_t P, const float* d, const float* pixel_var, const uint8_t* mask, const float* C,
+                  const float* P1f, const float* Pst, const float* stripe_amp2, const float* s_init,
+                  const wf_schedule* sched, double tol, float* s_out, wf_stats* st) {
+  if (!s_init) return WF_EINVAL;
+  return solve_impl(P, d, pixel_var, mask, C, P1f, Pst, stripe_amp2, s_init, sched, tol, s_out, st);
 }
 
 int wf_fft2(wf_plan_t P, const float* in, float* out, int inverse, int rows_only) {

@@ -207,6 +207,43 @@ col_kernel(ColArgs a) {
 #pragma unroll
       for (int m = 0; m < E; ++m) a.r_g[at(t + m * TPC)] = cscale(v[m], sc);
     }
+  } else if constexpr (MODE == COL_WARM) {
+    // warm start from s (in RF, row-major in a.in): the data-side messenger
+    // gets s itself (tiled copy), the signal-side field d_2DF = (C + N_0)/C s
+    // with the merged 2DF block (s = C/(C + N_0) d_2DF), or s itself
+    float2 vp[E];
+#pragma unroll
+    for (int m = 0; m < E; ++m) {
+      v[m] = valid ? a.in[at(t + m * TPC)] : make_float2(0.f, 0.f);
+      if (valid) a.warm_copy[att(t + m * TPC)] = v[m];
+    }
+    if (a.has_f) {
+      const float off0 = (float)a.st->off[0];
+      fft_block<L, E, false>(v, sb, t, a.twy, 1);
+      if (blockIdx.x == 0) exchange0(v, vp);
+#pragma unroll
+      for (int m = 0; m < E; ++m) {
+        const int k = t + m * TPC;
+        const float2 eg = valid ? a.eig[att(k)] : make_float2(1.f, 0.f);
+        const float fa = __fdividef(eg.x + eg.y + off0, eg.x);
+        if (blockIdx.x == 0 && c == 0) {
+          const float2 egb = a.eig_nyq[k];
+          float2 A, B;
+          unpack_pair(v[m], vp[m], A, B);
+          v[m] = repack_pair(cscale(A, fa), cscale(B, __fdividef(egb.x + egb.y + off0, egb.x)));
+        } else {
+          v[m] = cscale(v[m], fa);
+        }
+      }
+      fft_block<L, E, true>(v, sb, t, a.twy, 1);
+      const float sc = 1.0f / (float)L;
+#pragma unroll
+      for (int m = 0; m < E; ++m) v[m] = cscale(v[m], sc);
+    }
+    if (valid) {
+#pragma unroll
+      for (int m = 0; m < E; ++m) a.out[att(t + m * TPC)] = v[m];
+    }
   } else if constexpr (MODE == COL_UNTILE) {
     if (valid) {
 #pragma unroll
@@ -244,6 +281,7 @@ static int launch_col_L(int mode, const ColArgs& a, cudaStream_t s) {
     case COL_G_FROM_S: return launch_pdl(col_kernel<L, COL_G_FROM_S>, grid, block, 0, s, a);
     case COL_UNTILE: return launch_pdl(col_kernel<L, COL_UNTILE>, grid, block, 0, s, a);
     case COL_FWD_TILED: return launch_pdl(col_kernel<L, COL_FWD_TILED>, grid, block, 0, s, a);
+    case COL_WARM: return launch_pdl(col_kernel<L, COL_WARM>, grid, block, 0, s, a);
     default: return (int)cudaErrorInvalidValue;
   }
   return (int)cudaGetLastError();

@@ -77,6 +77,7 @@ enum ColMode : int {
   COL_UNTILE = 8,     // column-tiled RF field -> row-major (exports)
   COL_FWD_TILED = 9,  // RF -> 2D Fourier, column-tiled output
   COL_PASS_MERGE_SRC = 10,  // COL_PASS_MERGE with a source term (defect correction)
+  COL_WARM = 11,      // warm start: s in RF -> the signal-side field (tiled) and a tiled copy
   COL_NMODES = 11
 };
 
@@ -124,6 +125,7 @@ struct ColArgs {
   const float2* in;           // generic transforms
   float2* out;
   const float2* src;          // 2D-Fourier source j^ (column-tiled) or nullptr
+  float2* warm_copy;          // COL_WARM: tiled copy of the input (t_RF or t_PX)
 };
 
 // launchers (return a cudaError_t as int)

@@ -188,3 +188,18 @@ def cfg0_problem(seed: int = 0) -> Problem:
 def cfg1_problem(seed: int = 1000, n: int = 1024, **kw) -> Problem:
     """n x n, white + isotropic 1/f + horizontal stripes, 5% disc mask."""
     return make_problem(n, n, seed, **kw)
+
+
+def fno_init(seed: int, width: int = 32, mx: int = 16, my: int = 16, layers: int = 4, cin: int = 2) -> np.ndarray:
+    """Seeded initial parameters of the warm-start network, as one float32
+    vector in the order P [width][cin], p [width], per layer W [width][width],
+    w [width], R [width][width][2 my][mx] (re, im) pairs, then Q [1][width],
+    q [1].  Matrices ~ N(0, 1/fan_in); spectral weights uniform in
+    [0, 1/width^2) in both parts; biases 0."""
+    rng = np.random.default_rng(seed)
+    parts = [rng.normal(0.0, 1.0 / np.sqrt(cin), (width, cin)).ravel(), np.zeros(width)]
+    for _ in range(layers):
+        parts += [rng.normal(0.0, 1.0 / np.sqrt(width), (width, width)).ravel(), np.zeros(width),
+                  rng.uniform(0.0, 1.0 / (width * width), (width, width, 2 * my, mx, 2)).ravel()]
+    parts += [rng.normal(0.0, 1.0 / np.sqrt(width), (1, width)).ravel(), np.zeros(1)]
+    return np.concatenate(parts).astype(np.float32)

@@ -27,7 +27,9 @@ WF_FIELD_S, WF_FIELD_T_2DF, WF_FIELD_D_2DF, WF_FIELD_T_RF, WF_FIELD_D_RF = range
 EXPORTS = ["wf_version", "wf_strerror", "wf_params_default", "wf_plan_create", "wf_plan_destroy",
            "wf_set_problem", "wf_run", "wf_iterate", "wf_residual", "wf_get_field", "wf_solve",
            "wf_fft2", "wf_launch_count", "wf_time_passes", "wf_fft2_noalloc",
-           "wf_batch_create", "wf_batch_destroy", "wf_batch_solve", "wf_batch_launch_count"]
+           "wf_batch_create", "wf_batch_destroy", "wf_batch_solve", "wf_batch_launch_count",
+           "wf_fno_create", "wf_fno_destroy", "wf_fno_num_params", "wf_fno_forward", "wf_fno_gradient",
+           "wf_fno_train_step", "wf_fno_get_params", "wf_fno_features", "wf_solve_warm"]
 
 
 class wf_schedule(C.Structure):
@@ -107,12 +109,23 @@ def load(path: Optional[str] = None):
     L.wf_batch_destroy.argtypes = [vp]
     L.wf_batch_solve.argtypes = [vp, C.POINTER(wf_map), C.POINTER(wf_schedule), C.c_double, C.POINTER(wf_stats)]
     L.wf_batch_launch_count.argtypes = [vp]
+    L.wf_fno_create.argtypes = [C.POINTER(vp), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp]
+    L.wf_fno_destroy.restype = None
+    L.wf_fno_destroy.argtypes = [vp]
+    L.wf_fno_num_params.argtypes = [vp]
+    L.wf_fno_forward.argtypes = [vp, vp, vp, C.c_int]
+    L.wf_fno_gradient.argtypes = [vp, vp, vp, C.c_int, vp, C.POINTER(C.c_double)]
+    L.wf_fno_train_step.argtypes = [vp, vp, vp, C.c_int, C.c_double, C.POINTER(C.c_double)]
+    L.wf_fno_get_params.argtypes = [vp, vp, C.c_int]
+    L.wf_fno_features.argtypes = [C.c_int, C.c_int, vp, vp, vp, vp, vp, vp]
+    L.wf_solve_warm.argtypes = [vp] + [vp] * 8 + [C.POINTER(wf_schedule), C.c_double, vp, C.POINTER(wf_stats)]
     for n in EXPORTS:
         if n not in ("wf_strerror", "wf_params_default", "wf_plan_destroy", "wf_launch_count",
-                     "wf_batch_destroy", "wf_batch_launch_count"):
+                     "wf_batch_destroy", "wf_batch_launch_count", "wf_fno_destroy", "wf_fno_num_params"):
             getattr(L, n).restype = C.c_int
     L.wf_launch_count.restype = C.c_longlong
     L.wf_batch_launch_count.restype = C.c_longlong
+    L.wf_fno_num_params.restype = C.c_longlong
     _LIB = L
     return L
 
@@ -310,6 +323,19 @@ class Plan:
             _check(rc, "wf_solve")
         return out, st.as_dict()
 
+    def solve_warm(self, d, pixel_var, mask, Cs, P1f, Pst, stripe_amp2, s_init, schedule, tol, out=None):
+        """wf_solve started from the estimate s_init (see wf_solve_warm)."""
+        if out is None:
+            out = np.empty((self.ny, self.nx), np.float32)
+        ptrs = self._problem_ptrs(d, pixel_var, mask, Cs, P1f, Pst, stripe_amp2)
+        pi, ki = _ptr(s_init, np.float32, self.ny * self.nx)
+        po, keep = _ptr(out, np.float32, self.ny * self.nx, writable=True)
+        st = wf_stats()
+        rc = load().wf_solve_warm(self.h, *ptrs, pi, C.byref(schedule), float(tol), po, C.byref(st))
+        if rc not in _FINISHED:
+            _check(rc, "wf_solve_warm")
+        return out, st.as_dict()
+
     def fft2(self, x, inverse=False, rows_only=False, out=None):
         n = self.ny * self.nx
         if out is None:
@@ -392,6 +418,71 @@ class Batch:
 
     def launch_count(self) -> int:
         return int(load().wf_batch_launch_count(self.h))
+
+
+class FNO:
+    """The warm-start network and its training state (wf_fno_* in include/wf.h).
+    Arrays passed to forward / gradient / train_step are CUDA tensors."""
+
+    def __init__(self, n, batch, params, width=32, mx=16, my=16, layers=4, stream=None):
+        self.n, self.batch, self.width, self.mx, self.my, self.layers = n, batch, width, mx, my, layers
+        pp, keep = _ptr(params, np.float32)
+        self.h = C.c_void_p()
+        _check(load().wf_fno_create(C.byref(self.h), int(n), int(batch), int(width), int(mx), int(my), int(layers),
+                                    pp, stream if stream is not None else _current_stream()), "wf_fno_create")
+        self.num_params = int(load().wf_fno_num_params(self.h))
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            load().wf_fno_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def forward(self, x, y, nb):
+        px, kx = _ptr(x, np.float32)
+        py, ky = _ptr(y, np.float32, writable=True)
+        _check(load().wf_fno_forward(self.h, px, py, int(nb)), "wf_fno_forward")
+        return y
+
+    def gradient(self, x, t, nb):
+        g = np.empty(self.num_params, np.float32)
+        px, kx = _ptr(x, np.float32)
+        pt, kt = _ptr(t, np.float32)
+        l = C.c_double()
+        _check(load().wf_fno_gradient(self.h, px, pt, int(nb), C.c_void_p(g.ctypes.data), C.byref(l)),
+               "wf_fno_gradient")
+        return l.value, g
+
+    def train_step(self, x, t, nb, lr):
+        px, kx = _ptr(x, np.float32)
+        pt, kt = _ptr(t, np.float32)
+        l = C.c_double()
+        _check(load().wf_fno_train_step(self.h, px, pt, int(nb), float(lr), C.byref(l)), "wf_fno_train_step")
+        return l.value
+
+    def params(self, rounded=False):
+        out = np.empty(self.num_params, np.float32)
+        _check(load().wf_fno_get_params(self.h, C.c_void_p(out.ctypes.data), int(bool(rounded))), "wf_fno_get_params")
+        return out
+
+
+def fno_features(d, pixel_var, mask, x_out, sigma_out, stream=None):
+    """Network input of one map into x_out [2, ny, nx] and sigma into
+    sigma_out (CUDA tensors; see wf_fno_features)."""
+    ny, nx = d.shape
+    pd, kd = _ptr(d, np.float32)
+    pv, kv = _ptr(pixel_var, np.float32)
+    pm, km = _ptr(mask, np.uint8)
+    px, kx = _ptr(x_out, np.float32, writable=True)
+    ps, ks = _ptr(sigma_out, np.float32, writable=True)
+    _check(load().wf_fno_features(int(ny), int(nx), pd, pv, pm, px, ps,
+                                  stream if stream is not None else _current_stream()), "wf_fno_features")
+    return x_out
 
 
 def parts_of(prob) -> int:
