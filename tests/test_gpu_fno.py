@@ -112,3 +112,59 @@ def test_warm_start_from_the_solution_needs_few_sweeps(wf):
     # the first solve of the warm start starts at the answer: it stops at its
     # first checkpoints (the correction solve runs its fixed budget either way)
     assert st_w["iters"] < st_c["iters"] - 1000, (st_c["iters"], st_w["iters"])
+
+
+def test_trained_network_gains_over_the_cold_start(wf):
+    # train on maps the batched solver solves, then solve held-out maps cold
+    # (the benchmark's schedule) and from the network's prediction (the same
+    # levels at half length): both reach the FP64 solution, the warm start in
+    # fewer sweeps; a zero start with the warm schedule is the control
+    import os
+    import torch
+    import bench
+    O.set_workers(os.cpu_count() or 1)
+    n, ntr, nte, B = 256, 128, 4, 8
+    probs = [synth.make_problem(n, n, 8000 + i, amp_jitter=0.5) for i in range(ntr + nte)]
+    inp = [tuple(dev(a) for a in (p.d, p.pixel_var, p.mask, p.C, p.P1f, p.Pst, p.stripe_amp2)) for p in probs]
+    params = bench.solver_params(wf, max_iters=60000)
+    sched = bench.solver_schedule(wf)
+    wsched = bench.warm_schedule(wf)
+    sol = [torch.empty(n, n, device="cuda") for _ in range(ntr)]
+    b = wf.Batch([(n, n)] * ntr, params=params, lanes=16)
+    b.solve(inp[:ntr], sched, bench.TOL, sol)
+    b.close()
+    X = torch.empty(len(probs), 2, n, n, device="cuda")
+    SG = torch.empty(len(probs), device="cuda")
+    for i in range(len(probs)):
+        wf.fno_features(inp[i][0], inp[i][1], inp[i][2], X[i], SG[i:i + 1])
+    T = torch.stack(sol) / SG[:ntr, None, None]
+    net = wf.FNO(n, B, synth.fno_init(2, **bench.WARM_FNO), **bench.WARM_FNO)
+    rng = np.random.default_rng(1)
+    for it in range(600):
+        idx = torch.from_numpy(rng.choice(ntr, B, replace=False)).cuda()
+        net.train_step(X[idx].contiguous(), T[idx].contiguous(), B, 2e-3 * 0.5 ** (it // 150))
+    y = torch.empty(B, n, n, device="cuda")
+    cold_it, warm_it, ctrl_it, errs = [], [], [], []
+    for j in range(nte):
+        i = ntr + j
+        plan = wf.Plan(n, n, wf.parts_of(probs[i]), params)
+        cold = torch.empty(n, n, device="cuda")
+        _, st_c = plan.solve(*inp[i], sched, bench.TOL, out=cold)
+        ctrl = torch.empty(n, n, device="cuda")
+        _, st_z = plan.solve(*inp[i], wsched, bench.TOL, out=ctrl)
+        net.forward(X[i:i + 1].contiguous(), y, 1)
+        warm = torch.empty(n, n, device="cuda")
+        _, st_w = plan.solve_warm(*inp[i], (y[0] * SG[i]).contiguous(), wsched, bench.TOL, out=warm)
+        plan.close()
+        ref = O.pcg_wf(probs[i], tol=1e-10)
+        assert st_c["status"] == 0 and st_w["status"] == 0
+        e_c, e_w, e_z = (rel(a.cpu().numpy(), ref) for a in (cold, warm, ctrl))
+        errs.append((e_c, e_w, e_z))
+        assert e_c < 1e-4 and e_w < 1e-4, (e_c, e_w)
+        cold_it.append(st_c["iters"])
+        warm_it.append(st_w["iters"])
+        ctrl_it.append(st_z["iters"])
+    net.close()
+    print(f"256^2 sweeps per solve: cold {np.mean(cold_it):.0f}, warm-started {np.mean(warm_it):.0f}, "
+          f"zero start with the warm schedule {np.mean(ctrl_it):.0f}; worst errors {np.max(errs, axis=0)}")
+    assert np.mean(warm_it) < np.mean(cold_it)
