@@ -150,6 +150,12 @@ typedef struct {
  *                  place.  With refine > 0 a stalled first solve goes on to
  *                  the corrections, and wf_solve then reports WF_OK when the
  *                  refined s passes the stop test.  0 (default): never.
+ *  autotune        1 (default): the first problem a plan loads times both
+ *                  compiled shapes of each pass (values per thread) on the
+ *                  plan's buffers and keeps the faster, cached per device and
+ *                  map shape for the process (see wf_plan_shapes); 0: the
+ *                  first shapes; 2: the second shapes, untimed.  The shape
+ *                  changes only the rounding order.
  *  refine_lam1_iters with a cap and a fixed schedule, each correction runs
  *                  the schedule's levels (lambda > 1) for at most
  *                  refine_max_iters - refine_lam1_iters sweeps and then
@@ -177,7 +183,7 @@ typedef struct {
   int refine_max_iters;
   int refine_lam1_iters;
   int stall_checks;
-  int reserved;
+  int autotune;
 } wf_params;
 
 /* Results of a solve. */
@@ -309,6 +315,13 @@ WF_API int wf_fft2(wf_plan_t plan, const float* in, float* out, int inverse,
  * difference of two calls).  Returns -1 for a NULL plan.
  */
 WF_API long long wf_launch_count(wf_plan_t plan);
+
+/*
+ * wf_plan_shapes -- values per thread of the row pass and of the column pass
+ * the plan uses (set by the autotuner when the first problem is loaded).
+ * Either pointer may be NULL.
+ */
+WF_API int wf_plan_shapes(wf_plan_t plan, int* row_values, int* col_values);
 
 /*
  * wf_time_passes -- measurement aid: at fixed lambda, capture n row passes

@@ -14,6 +14,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "../../include/wf.h"
@@ -58,6 +61,11 @@ struct wf_plan_s {
   // captured and replayed on the plan's own stream (the caller's stream may
   // be the legacy default stream, which cannot be captured)
   cudaStream_t gstream = nullptr;
+  // pass shapes (values per thread) picked by the autotuner, and a copy of
+  // the state it restores after timing
+  int row_variant = 0, col_variant = 0;
+  bool tuned = false;
+  WfState* st_save = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   // two cached chunk graphs: a solve and its correction solves alternate
   struct ChunkGraph {
@@ -162,6 +170,7 @@ void wf_params_default(wf_params* p) {
   p->residual_every = 10;
   p->max_iters = 200000;
   p->check_every = 8;
+  p->autotune = 1;
 }
 
 void wf_plan_destroy(wf_plan_t P) {
@@ -195,7 +204,7 @@ int wf::check_plan_args(int ny, int nx, unsigned parts, const wf_params* p) {
     return WF_EINVAL;
   if (!(prm.tol_u_scale > 0.0) || (prm.merge_2df != 0 && prm.merge_2df != 1)) return WF_EINVAL;
   if (prm.refine < 0 || prm.refine > 8 || !(prm.refine_tol_scale >= 1.0) || prm.refine_max_iters < 0 ||
-      prm.refine_lam1_iters < 0 || prm.stall_checks < 0)
+      prm.refine_lam1_iters < 0 || prm.stall_checks < 0 || prm.autotune < 0 || prm.autotune > 2)
     return WF_EINVAL;
   return WF_OK;
 }
@@ -219,6 +228,7 @@ int wf_plan_create(wf_plan_t* out, int ny, int nx, unsigned parts, const wf_para
   P->has_rf = parts & WF_PART_STRIPE;
   P->merge = P->has_f && prm.merge_2df;
   P->p = prm;
+  if (prm.autotune == 2) P->row_variant = P->col_variant = 1;  // the second shapes, untimed
   P->stream = (cudaStream_t)stream;
   P->nrow = row_grid(nx, ny);
   const size_t npx = (size_t)ny * nx, nh = (size_t)ny * P->M;
@@ -245,6 +255,7 @@ int wf_plan_create(wf_plan_t* out, int ny, int nx, unsigned parts, const wf_para
   AL(P->r_q, nh);
   AL(P->part, (size_t)3 * P->nrow + 4 * 256 + 64);
   AL(P->st, (size_t)1);
+  AL(P->st_save, (size_t)1);
   AL(P->lam_sched, (size_t)260);
   AL(P->it_sched, (size_t)260);
   AL(P->stg_d, npx);
@@ -310,6 +321,7 @@ int wf_plan_create(wf_plan_t* out, int ny, int nx, unsigned parts, const wf_para
 // ---------------------------------------------------------------- helpers
 static RowArgs row_args(wf_plan_s* P) {
   RowArgs a{};
+  a.variant = P->row_variant;
   a.ny = P->ny;
   a.nx = P->nx;
   a.has_rf = P->has_rf;
@@ -331,6 +343,7 @@ static RowArgs row_args(wf_plan_s* P) {
 
 static ColArgs col_args(wf_plan_s* P, int parity) {
   ColArgs a{};
+  a.variant = P->col_variant;
   a.ny = P->ny;
   a.nx = P->nx;
   a.has_rf = P->has_rf;
@@ -438,6 +451,108 @@ static int finish_status(unsigned err) {
   return WF_OK;
 }
 
+// ---------------------------------------------------------------- autotuner
+// Each pass has two compiled shapes (values per thread, so threads per row or
+// column); which is faster depends on the map size (measured: 4 values per
+// thread for rows of 512 and fewer pixels, 8 above; 8 for 512-long columns,
+// 16 above).  The first loaded problem of a plan times both shapes of each
+// pass -- graph-replayed launches on the plan's buffers, as wf_time_passes
+// does -- and keeps the faster one (the first unless the second wins by
+// more than 3%), cached per device, map shape and sweep form for the rest of
+// the process.  Results depend on the shape only through rounding order.
+
+namespace {
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, unsigned, int>, std::pair<int, int>> g_tune;
+}  // namespace
+
+// mean time of n launches of one pass with shape `variant`, in microseconds
+static int time_pass(wf_plan_s* P, int which, int variant, int n, cudaEvent_t e0, cudaEvent_t e1, double* us) {
+  const int rv = P->row_variant, cv = P->col_variant;
+  if (which == 0) P->row_variant = variant;
+  else P->col_variant = variant;
+  int rc = which == 0 ? enqueue_row_pass(P) : enqueue_col_pass(P, 0);  // un-captured: kernel attributes
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  if (!rc && cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = WF_ECUDA;
+  if (!rc) {
+    for (int i = 0; i < n && !rc; ++i) rc = which == 0 ? enqueue_row_pass(P) : enqueue_col_pass(P, 0);
+    cudaError_t ce = cudaStreamEndCapture(P->stream, &g);
+    if (!rc && (ce != cudaSuccess || cudaGraphInstantiate(&ge, g, 0) != cudaSuccess)) rc = WF_ECUDA;
+  }
+  float ms = 0.f;
+  if (!rc && (cudaGraphLaunch(ge, P->stream) != cudaSuccess || cudaEventRecord(e0, P->stream) != cudaSuccess ||
+              cudaGraphLaunch(ge, P->stream) != cudaSuccess || cudaEventRecord(e1, P->stream) != cudaSuccess ||
+              cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+    rc = WF_ECUDA;
+  if (ge) cudaGraphExecDestroy(ge);
+  if (g) cudaGraphDestroy(g);
+  P->row_variant = rv;
+  P->col_variant = cv;
+  if (rc) cudaGetLastError();
+  *us = 1000.0 * ms / n;
+  return rc;
+}
+
+static int autotune(wf_plan_s* P) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  const auto key = std::make_tuple(dev, P->ny, P->nx, P->parts, (int)P->merge);
+  // held while timing: plans of one shape on other threads wait for the
+  // answer instead of timing concurrently and possibly choosing differently
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(key);
+  if (it != g_tune.end()) {
+    P->row_variant = it->second.first;
+    P->col_variant = it->second.second;
+    P->tuned = true;
+    return WF_OK;
+  }
+  const bool two_rows = row_pass_e(P->M, 0) != row_pass_e(P->M, 1);
+  const bool two_cols = col_pass_e(P->ny, 0) != col_pass_e(P->ny, 1);
+  int rv = 0, cv = 0;
+  if (two_rows || two_cols) {
+    const int n = (int)std::min<size_t>(200, std::max<size_t>(8, (size_t)20000000 / ((size_t)P->ny * P->nx)));
+    cudaStream_t user = P->stream;
+    CK(cudaEventRecord(P->ev_in, user));
+    CK(cudaStreamWaitEvent(P->gstream, P->ev_in, 0));
+    P->stream = P->gstream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = WF_OK;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = WF_ECUDA;
+    // the passes run from the loaded problem's state at lambda = 1; state and
+    // fields are put back afterwards
+    if (!rc && cudaMemcpyAsync(P->st_save, P->st, sizeof(WfState), cudaMemcpyDeviceToDevice, P->stream) != cudaSuccess)
+      rc = WF_ECUDA;
+    if (!rc && launch_set_lambda(P->st, 1.0, 1, P->stream)) rc = WF_ECUDA;
+    double t[2][2] = {{0, 0}, {0, 0}};
+    for (int which = 0; which < 2 && !rc; ++which) {
+      if (!(which == 0 ? two_rows : two_cols)) continue;
+      for (int v = 0; v < 2 && !rc; ++v) rc = time_pass(P, which, v, n, e0, e1, &t[which][v]);
+    }
+    if (!rc) {
+      rv = (two_rows && t[0][1] < 0.97 * t[0][0]) ? 1 : 0;
+      cv = (two_cols && t[1][1] < 0.97 * t[1][0]) ? 1 : 0;
+    }
+    if (!rc && cudaMemcpyAsync(P->st, P->st_save, sizeof(WfState), cudaMemcpyDeviceToDevice, P->stream) != cudaSuccess)
+      rc = WF_ECUDA;
+    const size_t nhb = (size_t)P->ny * P->M * sizeof(float2);
+    for (float2* f : {P->f_x, P->f_d1, P->f_t1, P->f_y, P->f_t0})
+      if (!rc && f && cudaMemsetAsync(f, 0, nhb, P->stream) != cudaSuccess) rc = WF_ECUDA;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (cudaEventRecord(P->ev_out, P->gstream) != cudaSuccess || cudaStreamWaitEvent(user, P->ev_out, 0) != cudaSuccess)
+      rc = rc ? rc : WF_ECUDA;
+    P->stream = user;
+    if (rc) return rc;
+  }
+  P->row_variant = rv;
+  P->col_variant = cv;
+  P->tuned = true;
+  g_tune.emplace(key, std::make_pair(rv, cv));
+  return WF_OK;
+}
+
 extern "C" {
 
 int wf_set_problem(wf_plan_t P, const float* d, const float* pixel_var, const uint8_t* mask,
@@ -489,6 +604,7 @@ int wf_set_problem(wf_plan_t P, const float* d, const float* pixel_var, const ui
   P->has_src = false;
   const int st = finish_status(P->h_st->err);
   if (st != WF_OK) return st;
+  if (P->p.autotune == 1 && !P->tuned && (rc = autotune(P))) return rc;
   P->loaded = true;
   return WF_OK;
 }
@@ -927,6 +1043,13 @@ int wf_fft2(wf_plan_t P, const float* in, float* out, int inverse, int rows_only
 }
 
 long long wf_launch_count(wf_plan_t P) { return P ? P->launches : -1; }
+
+int wf_plan_shapes(wf_plan_t P, int* row_values, int* col_values) {
+  if (!P) return WF_EINVAL;
+  if (row_values) *row_values = row_pass_e(P->M, P->row_variant);
+  if (col_values) *col_values = col_pass_e(P->ny, P->col_variant);
+  return WF_OK;
+}
 
 int wf_time_passes(wf_plan_t P, double lam, int n, double* us_row, double* us_col) {
   if (!P || !P->loaded || n < 1 || !(lam >= 1.0) || !isfinite(lam)) return WF_EINVAL;

@@ -41,6 +41,7 @@ namespace {
 
 constexpr int kMaxMaps = 65536;
 constexpr int kMaxLanes = 64;
+constexpr int kNotRun = -1;
 
 void destroy(wf_batch_s* B) {
   for (wf_plan_t p : B->plans)
@@ -150,7 +151,7 @@ int wf_batch_solve(wf_batch_t B, const wf_map* maps, const wf_schedule* sched, d
     }
     for (int i : B->lane_maps[l]) {
       if (failed.load()) {
-        rc[i] = WF_ECUDA;
+        rc[i] = kNotRun;  // another map failed: this one is not solved
         continue;
       }
       const wf_map& m = maps[i];
@@ -169,6 +170,9 @@ int wf_batch_solve(wf_batch_t B, const wf_map* maps, const wf_schedule* sched, d
   // the caller's later work waits for every lane
   for (int l = 0; l < B->lanes; ++l)
     if (cudaStreamWaitEvent(B->user, B->lane_done[l], 0) != cudaSuccess) cudaGetLastError();
+  // the first real error (maps skipped after it do not mask it)
+  for (int i = 0; i < B->nmaps; ++i)
+    if (rc[i] != kNotRun && rc[i] != WF_OK && rc[i] != WF_ENOCONV && rc[i] != WF_ESTALL) return rc[i];
   int status = WF_OK;
   for (int i = 0; i < B->nmaps; ++i) {
     if (rc[i] != WF_OK && rc[i] != WF_ENOCONV && rc[i] != WF_ESTALL) return rc[i];

@@ -13,18 +13,23 @@ namespace wf {
 // Column pass geometry: W columns per CTA, TPC = L/E threads per column.
 // W is a whole number of column tiles (TMA bulk loads of contiguous tiles)
 // unless the tiles would not fit in shared memory, then half a tile.
-#ifndef WF_COL_E
-#define WF_COL_E 0  // 0: the default choice below; else values per thread (4, 8, 16)
-#endif
 constexpr size_t kMaxSmem = 227 * 1024;  // dynamic shared memory per CTA
 
-template <int L, int MODE>
+// Values per thread of the two shapes the autotuner chooses between (one
+// where both coincide): 16 measured fastest for columns of 1024 and more,
+// 8 for 512; 3 * 2^k columns take 12 or 24.
+template <int L>
+struct ColPassE {
+  static constexpr int v0 = (L % 3 == 0) ? ((L >= 1536) ? 24 : 12) : ((L >= 512) ? 16 : 8);
+  static constexpr int v1 = (L % 3 == 0 || L > 2048) ? v0 : ((L >= 512) ? 8 : (L >= 128 ? 16 : v0));
+};
+
+template <int L, int MODE, int EV>
 struct ColPassCfg {
   static constexpr bool T0 = (MODE == COL_PASS_2DF);
   static constexpr bool SRC = (MODE == COL_PASS_MERGE_SRC);
   static constexpr bool EXTRA = T0 || SRC;  // a third staged tile
-  static constexpr int E = (L % 3 == 0) ? ((L >= 1536) ? 24 : 12)
-                           : (WF_COL_E > 0 && WF_COL_E <= L / 2) ? WF_COL_E : ((L >= 512) ? 16 : 8);
+  static constexpr int E = EV;
   static constexpr int TPC = L / E;
   static constexpr int W_MIN = (TPC >= 32) ? 1 : 32 / TPC;  // at least one warp
   // widest staging that fits in 227 KB of shared memory
@@ -60,9 +65,9 @@ struct ColPassCfg {
 
 // Stage W columns of a column-tiled field: one bulk copy of whole tiles, or
 // 16-byte asynchronous copies of half-tile rows.
-template <int L, int MODE>
+template <int L, int MODE, int EV>
 __device__ __forceinline__ void stage_tiled(float2* dst, const float2* src, int col0, int ny, uint64_t* bar) {
-  using Cfg = ColPassCfg<L, MODE>;
+  using Cfg = ColPassCfg<L, MODE, EV>;
   if constexpr (Cfg::TILED) {
     if (threadIdx.x == 0) bulk_g2s(dst, src + tidx(0, col0, ny), (uint32_t)(L * Cfg::W * 8), bar);
   } else {
@@ -91,10 +96,10 @@ __device__ __forceinline__ void tile_load_rowmajor(float2* dst, const float2* sr
 // The column pass (Sec. 2 / Appendix A: the 2D-Fourier updates between the
 // forward and inverse column DFTs).  The messenger tile and the (C, P1f)
 // tile are staged in shared memory before the transform begins.
-template <int L, int MODE>
-__global__ void __launch_bounds__(ColPassCfg<L, MODE>::THREADS)
+template <int L, int MODE, int EV>
+__global__ void __launch_bounds__(ColPassCfg<L, MODE, EV>::THREADS)
 col_pass_kernel(ColArgs a) {
-  using Cfg = ColPassCfg<L, MODE>;
+  using Cfg = ColPassCfg<L, MODE, EV>;
   constexpr int E = Cfg::E, TPC = Cfg::TPC, W = Cfg::W;
   extern __shared__ __align__(16) unsigned char smem[];
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem);
@@ -122,7 +127,7 @@ col_pass_kernel(ColArgs a) {
   // twiddle table, fixed during a solve, on barrier 1
   if (threadIdx.x == 0)
     mbar_expect_tx(&bar[1], (Cfg::TILED ? (uint32_t)Cfg::tile : 0u) + (Cfg::TWS ? (uint32_t)(L * 8) : 0u));
-  stage_tiled<L, MODE>(s_eig, a.eig, col0, a.ny, &bar[1]);
+  stage_tiled<L, MODE, EV>(s_eig, a.eig, col0, a.ny, &bar[1]);
   if constexpr (Cfg::TWS)
     if (threadIdx.x == 0) bulk_g2s(s_tw, a.twy, (uint32_t)(L * 8), &bar[1]);
   cp_async_commit();
@@ -137,9 +142,9 @@ col_pass_kernel(ColArgs a) {
   // the messenger tile (and the source tile) on barrier 0
   if (threadIdx.x == 0)
     mbar_expect_tx(&bar[0], Cfg::TILED ? (uint32_t)(Cfg::tile * (Cfg::SRC ? 2 : 1)) : 0u);
-  stage_tiled<L, MODE>(s_y, a.f_y, col0, a.ny, &bar[0]);
+  stage_tiled<L, MODE, EV>(s_y, a.f_y, col0, a.ny, &bar[0]);
   cp_async_commit();
-  if constexpr (Cfg::SRC) stage_tiled<L, MODE>(s_t0, a.src, col0, a.ny, &bar[0]);
+  if constexpr (Cfg::SRC) stage_tiled<L, MODE, EV>(s_t0, a.src, col0, a.ny, &bar[0]);
   if constexpr (Cfg::T0) tile_load_rowmajor<L, W, Cfg::THREADS>(s_t0, a.f_t0, col0, ncols);
   cp_async_commit();
   // link covariances of this lambda level (written by the controller)
@@ -264,9 +269,9 @@ col_pass_kernel(ColArgs a) {
   for (int m = 0; m < E; ++m) a.f_x[tidx(t + m * TPC, col, a.ny)] = cscale(v[m], sc);
 }
 
-template <int L, int MODE>
-static int launch_col_pass(const ColArgs& a, cudaStream_t s) {
-  using Cfg = ColPassCfg<L, MODE>;
+template <int L, int MODE, int EV>
+static int launch_col_pass_e(const ColArgs& a, cudaStream_t s) {
+  using Cfg = ColPassCfg<L, MODE, EV>;
   const int ncols = a.nx / 2;
   if (ncols % Cfg::W != 0) return (int)cudaErrorInvalidValue;
   constexpr size_t kBytes = Cfg::bytes;
@@ -274,11 +279,21 @@ static int launch_col_pass(const ColArgs& a, cudaStream_t s) {
   static std::once_flag once;
   static cudaError_t cfg_err = cudaSuccess;
   std::call_once(once, [] {
-    cfg_err = cudaFuncSetAttribute(col_pass_kernel<L, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBytes);
+    cfg_err = cudaFuncSetAttribute(col_pass_kernel<L, MODE, EV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)kBytes);
   });
   if (cfg_err != cudaSuccess) return (int)cfg_err;
   const dim3 grid(ncols / Cfg::W), block(Cfg::THREADS);
-  return launch_pdl(col_pass_kernel<L, MODE>, grid, block, kBytes, s, a);
+  return launch_pdl(col_pass_kernel<L, MODE, EV>, grid, block, kBytes, s, a);
+}
+
+// a.variant selects the shape (0 or 1, ColPassE)
+template <int L, int MODE>
+static int launch_col_pass(const ColArgs& a, cudaStream_t s) {
+  if constexpr (ColPassE<L>::v1 != ColPassE<L>::v0) {
+    if (a.variant == 1) return launch_col_pass_e<L, MODE, ColPassE<L>::v1>(a, s);
+  }
+  return launch_col_pass_e<L, MODE, ColPassE<L>::v0>(a, s);
 }
 
 template <int L>
@@ -289,6 +304,26 @@ int launch_col_pass_any(int mode, const ColArgs& a, cudaStream_t s) {
     case COL_PASS_MERGE: return launch_col_pass<L, COL_PASS_MERGE>(a, s);
     case COL_PASS_MERGE_SRC: return launch_col_pass<L, COL_PASS_MERGE_SRC>(a, s);
     default: return (int)cudaErrorInvalidValue;
+  }
+}
+
+template <int L>
+static int col_e(int v) { return v == 1 ? ColPassE<L>::v1 : ColPassE<L>::v0; }
+
+int col_pass_e(int L, int v) {
+  switch (L) {
+    case 32: return col_e<32>(v);
+    case 64: return col_e<64>(v);
+    case 128: return col_e<128>(v);
+    case 256: return col_e<256>(v);
+    case 384: return col_e<384>(v);
+    case 512: return col_e<512>(v);
+    case 768: return col_e<768>(v);
+    case 1024: return col_e<1024>(v);
+    case 1536: return col_e<1536>(v);
+    case 2048: return col_e<2048>(v);
+    case 4096: return col_e<4096>(v);
+    default: return 0;
   }
 }
 

@@ -105,6 +105,7 @@ struct RowArgs {
   float2* out_px;
   const float2* src_px;       // source j on masked pixels (pairs) or nullptr
   float2* gm_out;             // S^-1 s on masked pixels (pairs), 0 elsewhere, or nullptr
+  int variant;                // row pass shape (0 or 1), chosen by the autotuner
 };
 
 struct ColArgs {
@@ -126,6 +127,7 @@ struct ColArgs {
   float2* out;
   const float2* src;          // 2D-Fourier source j^ (column-tiled) or nullptr
   float2* warm_copy;          // COL_WARM: tiled copy of the input (t_RF or t_PX)
+  int variant;                // column pass shape (0 or 1), chosen by the autotuner
 };
 
 // launchers (return a cudaError_t as int)
@@ -135,6 +137,9 @@ int row_grid(int nx, int ny);  // CTAs of a row pass (size of partial-sum arrays
 bool size_supported(int n);
 // argument checks of wf_plan_create (host only; WF_OK or a WF_E* code)
 int check_plan_args(int ny, int nx, unsigned parts, const wf_params* p);
+// values per thread of the row / column pass shape `variant` for a length
+int row_pass_e(int M, int variant);
+int col_pass_e(int L, int variant);
 
 // setup / control kernels
 struct SetupArgs {

@@ -183,24 +183,26 @@ row_kernel(RowArgs a) {
 // exchange steps need only warp barriers.  Short rows are packed several to
 // a warp.  One CTA = ROWS rows; the grid is ny / ROWS CTAs, small enough
 // units that the SMs finish within one row of each other.
-#ifndef WF_ROW_E
-#define WF_ROW_E 0  // 0: the default choice below; else values per thread (4, 8, 16)
-#endif
+// Values per thread of the two shapes the autotuner chooses between (one
+// where both coincide): 8 (two warps per 1024-point row) measured fastest at
+// 1024^2 and above, 4 at 512^2 and below; 3 * 2^k rows take 12.
 template <int M>
+struct RowPassE {
+  static constexpr int v0 = (M % 3 == 0) ? 12 : 8;
+  static constexpr int v1 = (M % 3 == 0) ? 12 : 4;
+};
+template <int M, int EV>
 struct RowPassCfg {
-  // 8 values per thread (two warps per 1024-point row) measured fastest at
-  // 1024^2; the longest rows (2048 complex) then get 8 warps
-  static constexpr int E_DEF = 8;
-  static constexpr int E = (M % 3 == 0) ? 12 : (WF_ROW_E > 0 && WF_ROW_E <= M / 2) ? WF_ROW_E : E_DEF;
+  static constexpr int E = EV;
   static constexpr int TPF = M / E;
   static constexpr int ROWS = (TPF >= 32) ? 1 : 32 / TPF;
   static constexpr int THREADS = ROWS * TPF;
   static constexpr bool WARP = (THREADS == 32);
 };
 
-template <int M, int MODE>
+template <int M, int MODE, int EV>
 struct RowPassSmem {
-  static constexpr int ROWS = RowPassCfg<M>::ROWS;
+  static constexpr int ROWS = RowPassCfg<M, EV>::ROWS;
   static constexpr bool RF = (MODE == ROW_PASS_RF);
   static constexpr size_t a_off = 16;
   static constexpr size_t dn_off = a_off + (size_t)ROWS * M * 8;
@@ -237,11 +239,11 @@ __device__ __forceinline__ void gather_tiled_rows(float2* dst, const float2* src
 // copies; the first transform starts as soon as its own field is in.  Waits
 // are bounded; on a timeout the CTA records WF_ERR_TIMEOUT, drains its
 // copies (bounded) and returns.
-template <int M, int MODE>
-__global__ void __launch_bounds__(RowPassCfg<M>::THREADS)
+template <int M, int MODE, int EV>
+__global__ void __launch_bounds__(RowPassCfg<M, EV>::THREADS)
 row_pass_kernel(RowArgs a) {
-  using Cfg = RowPassCfg<M>;
-  using SM = RowPassSmem<M, MODE>;
+  using Cfg = RowPassCfg<M, EV>;
+  using SM = RowPassSmem<M, MODE, EV>;
   constexpr int E = Cfg::E, TPF = Cfg::TPF, ROWS = Cfg::ROWS, NT = Cfg::THREADS;
   constexpr bool W = Cfg::WARP;
   constexpr bool RF = SM::RF;
@@ -379,19 +381,29 @@ row_pass_kernel(RowArgs a) {
   }
 }
 
-template <int M, int MODE>
-static int launch_row_pass(const RowArgs& a, cudaStream_t s) {
-  using Cfg = RowPassCfg<M>;
-  constexpr size_t bytes = RowPassSmem<M, MODE>::bytes;
+template <int M, int MODE, int EV>
+static int launch_row_pass_e(const RowArgs& a, cudaStream_t s) {
+  using Cfg = RowPassCfg<M, EV>;
+  constexpr size_t bytes = RowPassSmem<M, MODE, EV>::bytes;
   // once per instantiation and process (plans may run on several host threads)
   static std::once_flag once;
   static cudaError_t cfg_err = cudaSuccess;
   std::call_once(once, [] {
-    cfg_err = cudaFuncSetAttribute(row_pass_kernel<M, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cfg_err = cudaFuncSetAttribute(row_pass_kernel<M, MODE, EV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)bytes);
   });
   if (cfg_err != cudaSuccess) return (int)cfg_err;
   const dim3 grid((a.ny + Cfg::ROWS - 1) / Cfg::ROWS), block(Cfg::THREADS);
-  return launch_pdl(row_pass_kernel<M, MODE>, grid, block, bytes, s, a);
+  return launch_pdl(row_pass_kernel<M, MODE, EV>, grid, block, bytes, s, a);
+}
+
+// a.variant selects the shape (0 or 1, RowPassE)
+template <int M, int MODE>
+static int launch_row_pass(const RowArgs& a, cudaStream_t s) {
+  if constexpr (RowPassE<M>::v1 != RowPassE<M>::v0) {
+    if (a.variant == 1) return launch_row_pass_e<M, MODE, RowPassE<M>::v1>(a, s);
+  }
+  return launch_row_pass_e<M, MODE, RowPassE<M>::v0>(a, s);
 }
 
 template <int M>
@@ -447,6 +459,26 @@ int row_grid(int nx, int ny) {
     default: r = 1;
   }
   return (ny + r - 1) / r;
+}
+
+template <int M>
+static int row_e(int v) { return v == 1 ? RowPassE<M>::v1 : RowPassE<M>::v0; }
+
+int row_pass_e(int M, int v) {
+  switch (M) {
+    case 16: return row_e<16>(v);
+    case 32: return row_e<32>(v);
+    case 64: return row_e<64>(v);
+    case 128: return row_e<128>(v);
+    case 192: return row_e<192>(v);
+    case 256: return row_e<256>(v);
+    case 384: return row_e<384>(v);
+    case 512: return row_e<512>(v);
+    case 768: return row_e<768>(v);
+    case 1024: return row_e<1024>(v);
+    case 2048: return row_e<2048>(v);
+    default: return 0;
+  }
 }
 
 bool size_supported(int n) {

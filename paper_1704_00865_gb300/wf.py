@@ -29,7 +29,7 @@ EXPORTS = ["wf_version", "wf_strerror", "wf_params_default", "wf_plan_create", "
            "wf_fft2", "wf_launch_count", "wf_time_passes", "wf_fft2_noalloc",
            "wf_batch_create", "wf_batch_destroy", "wf_batch_solve", "wf_batch_launch_count",
            "wf_fno_create", "wf_fno_destroy", "wf_fno_num_params", "wf_fno_forward", "wf_fno_gradient",
-           "wf_fno_train_step", "wf_fno_get_params", "wf_fno_features", "wf_solve_warm"]
+           "wf_fno_train_step", "wf_fno_get_params", "wf_fno_features", "wf_solve_warm", "wf_plan_shapes"]
 
 
 class wf_schedule(C.Structure):
@@ -43,7 +43,7 @@ class wf_params(C.Structure):
                 ("split_w", C.c_double), ("tol_u_scale", C.c_double), ("residual_every", C.c_int), ("max_iters", C.c_int),
                 ("check_every", C.c_int), ("merge_2df", C.c_int), ("refine", C.c_int),
                 ("refine_tol_scale", C.c_double), ("refine_max_iters", C.c_int),
-                ("refine_lam1_iters", C.c_int), ("stall_checks", C.c_int), ("reserved", C.c_int)]
+                ("refine_lam1_iters", C.c_int), ("stall_checks", C.c_int), ("autotune", C.c_int)]
 
 
 class wf_stats(C.Structure):
@@ -118,6 +118,7 @@ def load(path: Optional[str] = None):
     L.wf_fno_train_step.argtypes = [vp, vp, vp, C.c_int, C.c_double, C.POINTER(C.c_double)]
     L.wf_fno_get_params.argtypes = [vp, vp, C.c_int]
     L.wf_fno_features.argtypes = [C.c_int, C.c_int, vp, vp, vp, vp, vp, vp]
+    L.wf_plan_shapes.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.wf_solve_warm.argtypes = [vp] + [vp] * 8 + [C.POINTER(wf_schedule), C.c_double, vp, C.POINTER(wf_stats)]
     for n in EXPORTS:
         if n not in ("wf_strerror", "wf_params_default", "wf_plan_destroy", "wf_launch_count",
@@ -175,8 +176,10 @@ def wf_params_default() -> wf_params:
 def make_params(theta=None, split_f=None, split_w=None, residual_every=None, max_iters=None,
                 check_every=None, merge_2df=None, tol_u_scale=None, split_fp=None,
                 refine=None, refine_tol_scale=None, refine_max_iters=None,
-                refine_lam1_iters=None, stall_checks=None) -> wf_params:
+                refine_lam1_iters=None, stall_checks=None, autotune=None) -> wf_params:
     p = wf_params_default()
+    if autotune is not None:
+        p.autotune = int(autotune)
     if stall_checks is not None:
         p.stall_checks = int(stall_checks)
     if refine_lam1_iters is not None:
@@ -348,6 +351,12 @@ class Plan:
 
     def launch_count(self) -> int:
         return int(load().wf_launch_count(self.h))
+
+    def shapes(self):
+        """(values per thread of the row pass, of the column pass)."""
+        r, c = C.c_int(), C.c_int()
+        _check(load().wf_plan_shapes(self.h, C.byref(r), C.byref(c)), "wf_plan_shapes")
+        return r.value, c.value
 
     def time_passes(self, lam: float, n: int):
         """Mean CUDA-event time (us) of the row pass and of the column pass."""

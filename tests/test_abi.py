@@ -50,6 +50,8 @@ def test_host_only_entry_points(lib):
     assert p.split_f == 0.5 and p.split_fp == 0.5 and p.split_w == 0.0
     assert p.residual_every == 10 and p.check_every == 8
     assert p.merge_2df == 1 and p.tol_u_scale == 1.0 and p.refine == 0 and p.refine_tol_scale == 100.0
+    assert p.autotune == 1 and p.stall_checks == 0 and p.refine_max_iters == 0
+    assert lib.wf_plan_shapes(None, None, None) == wf.WF_EINVAL
 
 
 @pytest.mark.parametrize("ny,nx,parts,code", [
@@ -69,7 +71,8 @@ def test_plan_create_rejects_bad_params(lib):
     from paper_1704_00865_gb300 import wf
     for kw in (dict(theta=(0.9, 1.5, 1.0)), dict(split_f=0.5, split_fp=0.5, merge_2df=0), dict(split_f=1.01, split_fp=0.0), dict(split_f=0.6, split_fp=0.6),
                dict(residual_every=0), dict(tol_u_scale=0.0), dict(refine=-1), dict(refine=9),
-               dict(refine_max_iters=-1), dict(refine_lam1_iters=-1), dict(stall_checks=-1)):
+               dict(refine_max_iters=-1), dict(refine_lam1_iters=-1), dict(stall_checks=-1),
+               dict(autotune=3)):
         p = wf.make_params(**kw)
         h = C.c_void_p()
         assert lib.wf_plan_create(C.byref(h), 64, 64, 7, C.byref(p), None) == wf.WF_EINVAL
