@@ -481,6 +481,20 @@ WF_API int wf_fno_features(int ny, int nx, const float* d, const float* pixel_va
                            float* x_out, float* sigma_out, void* stream);
 
 /*
+ * wf_inverse_noise -- approximately inverse-noise-weighted map N^-1 d (with a
+ * mask: zero on masked pixels, (P N P^T)^-1 d on the others), computed as a
+ * Wiener filter with the signal covariance set to S = alpha I (Sec. 4):
+ * N^-1 d ~ alpha^-1 [alpha (alpha I + N)^-1 d], relative error of order
+ * alpha / (smallest eigenvalue of N).  alpha > 0 (for example 1e-3 times the
+ * smallest pixel variance).  Arguments as for wf_solve without C; out (host
+ * or device, [ny][nx]) receives the weighted map; tol is the stop test of
+ * that filter.  Uses the plan's host-staging buffers for C and for s.
+ */
+WF_API int wf_inverse_noise(wf_plan_t plan, const float* d, const float* pixel_var, const uint8_t* mask,
+                            const float* P1f, const float* Pst, const float* stripe_amp2, double alpha,
+                            const wf_schedule* sched, double tol, float* out, wf_stats* stats);
+
+/*
  * wf_solve_warm -- wf_solve started from an estimate s_init of s (host or
  * device [ny][nx]) instead of zero: the messenger fields are set to s_init
  * in their own bases (t_RF = d_RF = s_init row-transformed; the signal-side

@@ -13,6 +13,8 @@ What it computes (Huffenberger 2017, arXiv:1704.00865):
                        restricted to unmasked pixels.
 * ``closed_form``   -- homogeneous noise: every part is diagonal in 2D Fourier
                        space and s_k = C_k / (C_k + N_k) d_k (Sec. 3.1).
+* ``inverse_noise_dense`` -- N^-1 d by its definition (dense, tiny maps): what
+                       the S = alpha I Wiener filter of Sec. 4 approximates.
 * ``Chain`` / ``messenger_solve`` -- the messenger iteration itself, eqs.
                        (2mess_t1)-(2mess_s) of Sec. 2 generalised to K parts
                        as Sec. 2 and Appendix A describe ("each additional
@@ -74,6 +76,7 @@ __all__ = [
     "cooling_levels", "apply_N", "apply_Sinv", "residual_terms", "pcg",
     "literal_residual", "pcg_wf", "chi2", "rel_l2", "DEFAULT_THETA",
     "ADAPTIVE_DEFAULT", "DEFAULT_SPLIT_F", "rel_terms", "to_basis", "from_basis",
+    "inverse_noise_dense",
 ]
 
 FFT_WORKERS = 1
@@ -593,6 +596,18 @@ def dense_wf(prob, return_parts: bool = False):
     if return_parts:
         return s, dict(S=S, Sinv=Sinv, N=N, Ninv=Ninv, um=um, A=A, b=b)
     return s
+
+
+def inverse_noise_dense(prob) -> np.ndarray:
+    """N^-1 d by its definition (Sec. 4, the S = alpha I remark computes it
+    approximately): with a mask, P^T (P N P^T)^-1 P d, zero on masked pixels;
+    dense Cholesky (tiny maps only)."""
+    from scipy.linalg import cho_factor, cho_solve
+    _, _, N, um = dense_matrices(prob)
+    d = np.asarray(prob.d, np.float64).ravel()
+    out = np.zeros(d.size)
+    out[um] = cho_solve(cho_factor(N[np.ix_(um, um)]), d[um])
+    return out.reshape(np.asarray(prob.d).shape)
 
 
 def dense_wf_alt(prob):

@@ -995,6 +995,27 @@ int wf_solve(wf_plan_t P, const float* d, const float* pixel_var, const uint8_t*
   return solve_impl(P, d, pixel_var, mask, C, P1f, Pst, stripe_amp2, nullptr, sched, tol, s_out, st);
 }
 
+int wf_inverse_noise(wf_plan_t P, const float* d, const float* pixel_var, const uint8_t* mask, const float* P1f,
+                     const float* Pst, const float* stripe_amp2, double alpha, const wf_schedule* sched, double tol,
+                     float* out, wf_stats* st) {
+  if (!P || !out || !sched || !(alpha > 0.0) || !isfinite(alpha) || alpha > 1e30) return WF_EINVAL;
+  const size_t npx = (size_t)P->ny * P->nx, nspec = (size_t)P->ny * (P->M + 1);
+  // S = alpha I: every signal eigenvalue alpha (the staging table of C)
+  CKI(launch_fill(P->stg_C, (float)alpha, nspec, P->stream));
+  P->launches += 1;
+  // s into the plan's device staging map, then scaled into out
+  int rc = solve_impl(P, d, pixel_var, mask, P->stg_C, P1f, Pst, stripe_amp2, nullptr, sched, tol, P->stg_io, st);
+  if (rc != WF_OK && rc != WF_ENOCONV && rc != WF_ESTALL) return rc;
+  // N^-1 d ~ alpha^-1 [alpha (alpha I + N)^-1 d]
+  const bool dev = is_device_ptr(out);
+  float* dst = dev ? out : P->stg_io;
+  CKI(launch_scale(dst, P->stg_io, (float)(1.0 / alpha), npx, P->stream));
+  P->launches += 1;
+  if (!dev) CK(cudaMemcpyAsync(out, dst, npx * sizeof(float), cudaMemcpyDeviceToHost, P->stream));
+  CK(cudaStreamSynchronize(P->stream));
+  return rc;
+}
+
 int wf_solve_warm(wf_plan_t P, const float* d, const float* pixel_var, const uint8_t* mask, const float* C,
                   const float* P1f, const float* Pst, const float* stripe_amp2, const float* s_init,
                   const wf_schedule* sched, double tol, float* s_out, wf_stats* st) {

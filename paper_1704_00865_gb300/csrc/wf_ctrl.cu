@@ -278,6 +278,25 @@ int launch_sub(float* y, const float* x, size_t n, cudaStream_t s) {
   return (int)cudaGetLastError();
 }
 
+__global__ void fill_kernel(float* y, float v, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) y[i] = v;
+}
+
+__global__ void scale_kernel(float* y, const float* x, float a, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    y[i] = a * x[i];
+}
+
+int launch_fill(float* y, float v, size_t n, cudaStream_t s) {
+  fill_kernel<<<SETUP_CTAS, SETUP_THREADS, 0, s>>>(y, v, n);
+  return (int)cudaGetLastError();
+}
+
+int launch_scale(float* y, const float* x, float a, size_t n, cudaStream_t s) {
+  scale_kernel<<<SETUP_CTAS, SETUP_THREADS, 0, s>>>(y, x, a, n);
+  return (int)cudaGetLastError();
+}
+
 int launch_set_lambda(WfState* st, double lam, int reset, cudaStream_t s) {
   set_lambda_kernel<<<1, 32, 0, s>>>(st, lam, reset);
   return (int)cudaGetLastError();

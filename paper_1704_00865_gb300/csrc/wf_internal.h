@@ -191,5 +191,8 @@ int launch_set_lambda(WfState* st, double lam, int reset, cudaStream_t s);
 int launch_pack_data(float4* dn_out, const float4* dn_in, const float2* rho, size_t npair,
                      double* part, WfState* st, cudaStream_t s);
 int launch_sub(float* y, const float* x, size_t n, cudaStream_t s);
+// y[i] = v;  y[i] = a x[i]
+int launch_fill(float* y, float v, size_t n, cudaStream_t s);
+int launch_scale(float* y, const float* x, float a, size_t n, cudaStream_t s);
 
 }  // namespace wf

@@ -29,7 +29,8 @@ EXPORTS = ["wf_version", "wf_strerror", "wf_params_default", "wf_plan_create", "
            "wf_fft2", "wf_launch_count", "wf_time_passes", "wf_fft2_noalloc",
            "wf_batch_create", "wf_batch_destroy", "wf_batch_solve", "wf_batch_launch_count",
            "wf_fno_create", "wf_fno_destroy", "wf_fno_num_params", "wf_fno_forward", "wf_fno_gradient",
-           "wf_fno_train_step", "wf_fno_get_params", "wf_fno_features", "wf_solve_warm", "wf_plan_shapes"]
+           "wf_fno_train_step", "wf_fno_get_params", "wf_fno_features", "wf_solve_warm", "wf_plan_shapes",
+           "wf_inverse_noise"]
 
 
 class wf_schedule(C.Structure):
@@ -118,6 +119,8 @@ def load(path: Optional[str] = None):
     L.wf_fno_train_step.argtypes = [vp, vp, vp, C.c_int, C.c_double, C.POINTER(C.c_double)]
     L.wf_fno_get_params.argtypes = [vp, vp, C.c_int]
     L.wf_fno_features.argtypes = [C.c_int, C.c_int, vp, vp, vp, vp, vp, vp]
+    L.wf_inverse_noise.argtypes = [vp] + [vp] * 6 + [C.c_double, C.POINTER(wf_schedule), C.c_double, vp,
+                                                     C.POINTER(wf_stats)]
     L.wf_plan_shapes.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.wf_solve_warm.argtypes = [vp] + [vp] * 8 + [C.POINTER(wf_schedule), C.c_double, vp, C.POINTER(wf_stats)]
     for n in EXPORTS:
@@ -324,6 +327,23 @@ class Plan:
         rc = load().wf_solve(self.h, *ptrs, C.byref(schedule), float(tol), po, C.byref(st))
         if rc not in _FINISHED:
             _check(rc, "wf_solve")
+        return out, st.as_dict()
+
+    def inverse_noise(self, d, pixel_var, mask, P1f, Pst, stripe_amp2, alpha, schedule, tol, out=None):
+        """Approximately N^-1 d through a Wiener filter with S = alpha I
+        (see wf_inverse_noise)."""
+        if out is None:
+            out = np.empty((self.ny, self.nx), np.float32)
+        ny, nx = self.ny, self.nx
+        nspec = ny * (nx // 2 + 1)
+        ptrs = [_ptr(d, np.float32, ny * nx), _ptr(pixel_var, np.float32, ny * nx), _ptr(mask, np.uint8, ny * nx),
+                _ptr(P1f, np.float32, nspec), _ptr(Pst, np.float32, nx // 2 + 1), _ptr(stripe_amp2, np.float32, ny)]
+        po, ko = _ptr(out, np.float32, ny * nx, writable=True)
+        st = wf_stats()
+        rc = load().wf_inverse_noise(self.h, *[p for p, _ in ptrs], float(alpha), C.byref(schedule), float(tol), po,
+                                     C.byref(st))
+        if rc not in _FINISHED:
+            _check(rc, "wf_inverse_noise")
         return out, st.as_dict()
 
     def solve_warm(self, d, pixel_var, mask, Cs, P1f, Pst, stripe_amp2, s_init, schedule, tol, out=None):

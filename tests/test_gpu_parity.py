@@ -284,3 +284,29 @@ def test_both_pass_shapes_match_the_oracle(wf, shape):
     r, c = tuned.shapes()
     assert r in {a for a, _ in seen} and c in {b for _, b in seen}
     tuned.close()
+
+
+@pytest.mark.parametrize("shape,kw", [((32, 64), dict()), ((64, 32), dict(one_over_f=False)),
+                                      ((32, 32), dict(stripes=False, one_over_f=False))])
+def test_inverse_noise_mode(wf, shape, kw):
+    # Sec. 4: with S = alpha I the filter gives N^-1 d ~ alpha^-1 WF(d); the
+    # library's result equals the oracle's exact filter at the same alpha, and
+    # is within O(alpha / lambda_min(N)) of N^-1 d itself
+    import copy
+    prob = synth.make_problem(*shape, 81, mask_frac=0.06, k_knee=4.0, k_knee_x=4.0, **kw)
+    _, _, N, um = O.dense_matrices(prob)
+    alpha = 1e-3 * float(np.linalg.eigvalsh(N[np.ix_(um, um)]).min())
+    sched = wf.make_schedule("fixed", O.cooling_levels(1e2, 5), [20] * 5)
+    extra = dict(split_w=0.5) if kw.get("one_over_f") is False and kw.get("stripes", True) else {}
+    plan = wf.Plan(*shape, wf.parts_of(prob), wf.make_params(refine=1, residual_every=10, max_iters=100000,
+                                                             tol_u_scale=20.0, **extra))
+    w, st = plan.inverse_noise(dev(prob.d), dev(prob.pixel_var), dev(prob.mask), dev(prob.P1f), dev(prob.Pst),
+                               dev(prob.stripe_amp2), alpha, sched, 1e-5)
+    plan.close()
+    assert st["status"] == 0, st
+    q = copy.deepcopy(prob)
+    q.C = np.full_like(prob.C, alpha)
+    assert rel(w, O.dense_wf(q) / alpha) < 1e-4
+    assert rel(w, O.inverse_noise_dense(prob)) < 3e-3
+    m = prob.mask.astype(bool)
+    assert np.linalg.norm(w[m]) < 1e-3 * np.linalg.norm(w)   # masked pixels carry no weight

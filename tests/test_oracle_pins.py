@@ -358,3 +358,25 @@ def test_pins_catch_planted_mistakes(monkeypatch, mutation):
     r = W.messenger_solve(p, schedule=W.fixed_schedule([30.0, 3.0], [20, 20]), tol=1e-12,
                           residual_every=10, max_iters=20000)
     assert r["status"] != "converged" or W.rel_l2(r["s"], s_d) > 1e-6
+
+
+def test_inverse_noise_weighting_definition():
+    # white noise only: N is diagonal, N^-1 d = d / pixel_var on unmasked pixels
+    prob = synth.make_problem(16, 16, 71, one_over_f=False, stripes=False, mask_frac=0.1)
+    w = O.inverse_noise_dense(prob)
+    m = prob.mask.astype(bool)
+    assert np.allclose(w[~m], prob.d[~m].astype(np.float64) / prob.pixel_var[~m], rtol=1e-12)
+    assert np.all(w[m] == 0.0)
+    # all parts: N (N^-1 d) = d on the unmasked pixels, and the S = alpha I
+    # Wiener filter divided by alpha approaches it at rate alpha
+    prob = synth.make_problem(16, 16, 72, mask_frac=0.1, k_knee=4.0, k_knee_x=4.0)
+    w = O.inverse_noise_dense(prob)
+    _, _, N, um = O.dense_matrices(prob)
+    assert np.allclose((N[np.ix_(um, um)] @ w.ravel()[um]), prob.d.ravel()[um].astype(np.float64), rtol=1e-9)
+    errs = []
+    lmin = np.linalg.eigvalsh(N[np.ix_(um, um)]).min()
+    for alpha in (1e-2 * lmin, 1e-3 * lmin):
+        q = synth.make_problem(16, 16, 72, mask_frac=0.1, k_knee=4.0, k_knee_x=4.0)
+        q.C[...] = alpha
+        errs.append(np.linalg.norm(O.dense_wf(q) / alpha - w) / np.linalg.norm(w))
+    assert errs[0] < 2e-2 and errs[1] < 2e-3 and errs[1] < 0.2 * errs[0]
