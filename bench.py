@@ -470,10 +470,14 @@ WARM_TEST = 16          # held-out maps
 WARM_STEPS = 1200       # Adam steps of WARM_BATCH maps, lr 2e-3 halved every quarter
 WARM_BATCH = 8
 WARM_FNO = dict(width=32, mx=16, my=16, layers=4)
-# the warm-started solve runs the headline levels at half length (starting at
-# lambda = 10 instead left 2 of 16 held-out maps above 1e-4 of the FP64
-# solution; these levels kept all 16 below it)
+# Where the prediction pays: with one long first solve (run to the stop
+# test, then one 4000-sweep correction) a warm start can shorten the
+# cooling -- the headline levels at half length (starting at lambda = 10
+# instead left 2 of 16 held-out maps above 1e-4 of the FP64 solution).
+# With the headline's short first solve and four corrections it saves
+# nothing: from zero, the same budgets reach the same accuracy.
 WARM_LAM, WARM_ITERS = [30.0, 10.0, 3.0, 1.5], [500, 1000, 1000, 1000]
+LONG_FIRST_SOLVE = dict(max_iters=60000, refine=1, refine_max_iters=4000)
 
 
 def warm_schedule(wf):
@@ -482,9 +486,10 @@ def warm_schedule(wf):
 
 def run_warm(args):
     """Train the FNO on maps the batched solver solves in this run, then solve
-    held-out maps cold (the headline schedule) and warm-started from the
-    network (half-length cooling levels), same solver settings otherwise; a
-    zero start with the warm schedule is the control."""
+    held-out maps cold and warm-started from the network: with the headline
+    solve settings, and with one long first solve (cold: the headline
+    schedule; warm: its levels at half length; control: the half-length
+    levels from zero)."""
     import torch
     from paper_1704_00865_gb300 import build, synth, wf
     build.build()
@@ -493,10 +498,11 @@ def run_warm(args):
     probs = [synth.make_problem(n, n, 7000 + i, amp_jitter=0.5) for i in range(WARM_TRAIN + WARM_TEST)]
     dev = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).cuda()
     inp = [tuple(dev(a) for a in (p.d, p.pixel_var, p.mask, p.C, p.P1f, p.Pst, p.stripe_amp2)) for p in probs]
-    params = solver_params(wf, max_iters=60000)
+    params = solver_params(wf)
+    params_long = solver_params(wf, **LONG_FIRST_SOLVE)
     sched = solver_schedule(wf)
     wsched = warm_schedule(wf)
-    # training targets: Wiener solutions of the training maps
+    # training targets: Wiener solutions of the training maps (headline solve)
     sol = [torch.empty(n, n, device="cuda") for _ in range(WARM_TRAIN)]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -522,48 +528,58 @@ def run_warm(args):
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     stream = torch.cuda.current_stream()
-    cold, warm, control = [], [], []
     y = torch.empty(WARM_BATCH, n, n, device="cuda")
     out = torch.empty(n, n, device="cuda")
-    for j in range(WARM_TEST):
-        i = WARM_TRAIN + j
-        plan = wf.Plan(n, n, wf.parts_of(probs[i]), params)
+    keys = ("cold", "warm", "cold_long", "warm_long", "control_long")
+    res = {k: [] for k in keys}
+
+    def timed(fn):
         for rep in range(2):  # the second of each pair is timed (graphs captured)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            _, st = plan.solve(*inp[i], sched, TOL, out=out)
+            st = fn()
             e1.record(stream)
             e1.synchronize()
-        cold.append((st["iters"], e0.elapsed_time(e1), st["status"]))
-        _, st = plan.solve(*inp[i], wsched, TOL, out=out)
-        control.append(st["iters"])
-        for rep in range(2):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
+        return st["iters"], e0.elapsed_time(e1), st["status"]
+
+    for j in range(WARM_TEST):
+        i = WARM_TRAIN + j
+
+        def predict():
             net.forward(X[i:i + 1].contiguous(), y, 1)   # inference inside the timed region
-            s_init = (y[0] * SG[i]).contiguous()
-            _, st = plan.solve_warm(*inp[i], s_init, wsched, TOL, out=out)
-            e1.record(stream)
-            e1.synchronize()
-        warm.append((st["iters"], e0.elapsed_time(e1), st["status"]))
-        plan.close()
+            return (y[0] * SG[i]).contiguous()
+
+        for key, prm in (("", params), ("_long", params_long)):
+            plan = wf.Plan(n, n, wf.parts_of(probs[i]), prm)
+            res["cold" + key].append(timed(lambda: plan.solve(*inp[i], sched, TOL, out=out)[1]))
+            ws = sched if key == "" else wsched
+            res["warm" + key].append(timed(lambda: plan.solve_warm(*inp[i], predict(), ws, TOL, out=out)[1]))
+            if key:
+                res["control_long"].append(timed(lambda: plan.solve(*inp[i], wsched, TOL, out=out)[1]))
+            plan.close()
     net.close()
-    c_ms = statistics.mean(c[1] for c in cold)
-    w_ms = statistics.mean(w[1] for w in warm)
-    line = {"metric": "warm-started WF solves/sec (FNO start, half-length cooling) vs cold start",
-            "value": round(1e3 / w_ms, 3), "unit": "solves/s", "n_gpus": 1, "steps": WARM_TEST, "warmup": 1,
-            "ms_per_step": round(w_ms, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 (network: fp16 weights, fp32 accumulate)", "data": "synthetic",
+
+    def summ(k):
+        v = res[k]
+        ms = statistics.mean(x[1] for x in v)
+        return {"solves_per_s": round(1e3 / ms, 3), "ms_per_solve": round(ms, 3),
+                "sweeps_per_solve": statistics.mean(x[0] for x in v), "status": [x[2] for x in v]}
+
+    S = {k: summ(k) for k in keys}
+    line = {"metric": "warm-started WF solves/sec (FNO prediction as the starting s) vs cold start",
+            "value": S["warm"]["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": WARM_TEST, "warmup": 1,
+            "ms_per_step": S["warm"]["ms_per_solve"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 (network: fp16 weights, fp32 accumulate)", "data": "synthetic",
             "config": {"workload": f"{n}x{n} maps, headline noise model, amplitudes x exp(U[-0.5,0.5]); "
                                    f"{WARM_TRAIN} training maps solved in the run, {WARM_TEST} held out",
                        "fno": WARM_FNO, "train_steps": WARM_STEPS, "batch": WARM_BATCH,
-                       "warm_schedule": {"lam": WARM_LAM, "iters": WARM_ITERS}},
-            "cold": {"solves_per_s": round(1e3 / c_ms, 3), "ms_per_solve": round(c_ms, 3),
-                     "sweeps_per_solve": statistics.mean(c[0] for c in cold), "status": [c[2] for c in cold]},
-            "warm": {"sweeps_per_solve": statistics.mean(w[0] for w in warm), "status": [w[2] for w in warm]},
-            "control_zero_start_warm_schedule": {"sweeps_per_solve": statistics.mean(control)},
-            "speedup_vs_cold": round(c_ms / w_ms, 3), "final_train_loss": round(loss, 4),
-            "data_seconds": round(t_data, 2), "train_seconds": round(t_train, 2)}
+                       "long_first_solve": LONG_FIRST_SOLVE,
+                       "warm_schedule_long": {"lam": WARM_LAM, "iters": WARM_ITERS}},
+            "headline_settings": {"cold": S["cold"], "warm": S["warm"],
+                                  "speedup": round(S["cold"]["ms_per_solve"] / S["warm"]["ms_per_solve"], 3)},
+            "long_first_solve": {"cold": S["cold_long"], "warm": S["warm_long"], "control": S["control_long"],
+                                 "speedup": round(S["cold_long"]["ms_per_solve"] / S["warm_long"]["ms_per_solve"], 3)},
+            "final_train_loss": round(loss, 4), "data_seconds": round(t_data, 2), "train_seconds": round(t_train, 2)}
     print(json.dumps(line))
     return 0
 
