@@ -595,7 +595,8 @@ def run_passes(args):
     n = args.size
     p = synth.make_problem(n, n, SEED + n)
     dev = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).cuda()
-    plan = wf.Plan(n, n, wf.parts_of(p), wf.make_params(merge_2df=1, split_f=SPLIT_F, split_fp=SPLIT_FP))
+    plan = wf.Plan(n, n, wf.parts_of(p), wf.make_params(merge_2df=1, split_f=SPLIT_F, split_fp=SPLIT_FP,
+                                                         dft_precision=args.dft_precision))
     plan.set_problem(*(dev(a) for a in (p.d, p.pixel_var, p.mask, p.C, p.P1f, p.Pst, p.stripe_amp2)))
     plan.iterate(1.0, 20)
     reps = max(20, int(2e8 / (n * n)))
@@ -607,10 +608,67 @@ def run_passes(args):
     row_gbs, col_gbs = ROW_BYTES_PER_PX * px / us_row / 1e3, COL_BYTES_PER_PX * px / us_col / 1e3
     sweep_gbs = (ROW_BYTES_PER_PX + COL_BYTES_PER_PX) * px / (us_row + us_col) / 1e3
     print(json.dumps({"metric": "row and column pass time", "map": [n, n], "launches_timed": reps,
+                      "dft_precision": PRECISIONS[args.dft_precision],
                       "us_row": round(us_row, 3), "us_col": round(us_col, 3),
                       "row_gbs": round(row_gbs, 1), "col_gbs": round(col_gbs, 1), "sweep_gbs": round(sweep_gbs, 1),
                       "sweep_frac_of_hbm": round(sweep_gbs / peak, 4), "hbm_peak_gbs": peak,
                       "pass_values_per_thread": {"row": rv, "col": cv}}))
+    return 0
+
+
+PRECISIONS = {0: "fp32", 1: "tf32 split (3 products)", 2: "tf32 (1 product)"}
+PRECISION_SIZES = (1024, 4096)
+
+
+def run_precision(args):
+    """The radix-16 stages of the column transforms in each arithmetic
+    (dft_precision 0, 1, 2): the benchmark's 1024^2 solve (solves/s, device
+    inputs, L2 flushed between solves) and the per-launch time of the column
+    pass at 1024^2 and 4096^2.  The errors against the FP64 oracle are
+    measured by tests/test_gpu_precision.py."""
+    import torch
+    from paper_1704_00865_gb300 import build, synth, wf
+    build.build()
+    wf.load()
+    prob = problem()
+    dev = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    inp = [dev(a) for a in (prob.d, prob.pixel_var, prob.mask, prob.C, prob.P1f, prob.Pst, prob.stripe_amp2)]
+    out = torch.empty(N, N, device="cuda")
+    flush = torch.empty(512 * 1024 * 1024 // 4, device="cuda")
+    stream = torch.cuda.current_stream()
+    sched = solver_schedule(wf)
+    res = {}
+    for prec, name in PRECISIONS.items():
+        plan = wf.Plan(N, N, wf.parts_of(prob), solver_params(wf, dft_precision=prec))
+        for _ in range(max(args.warmup, 1)):
+            plan.solve(*inp, sched, TOL, out=out)
+        ms, st = [], None
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = plan.solve(*inp, sched, TOL, out=out)[1]
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        plan.close()
+        entry = {"solves_per_s": round(1e3 * len(ms) / sum(ms), 4), "status": st["status"],
+                 "sweeps": st["iters"], "final_rel_rho_u": st["rel_rho_u"], "final_rel_rho_m": st["rel_rho_m"]}
+        for n in PRECISION_SIZES:
+            p = synth.make_problem(n, n, SEED + n)
+            pl = wf.Plan(n, n, wf.parts_of(p), wf.make_params(merge_2df=1, split_f=SPLIT_F, split_fp=SPLIT_FP,
+                                                               dft_precision=prec))
+            pl.set_problem(*(dev(a) for a in (p.d, p.pixel_var, p.mask, p.C, p.P1f, p.Pst, p.stripe_amp2)))
+            pl.iterate(1.0, 20)
+            us_row, us_col = pl.time_passes(1.0, max(20, int(2e8 / (n * n))))
+            pl.close()
+            entry[f"us_col_{n}"] = round(us_col, 3)
+            entry[f"us_row_{n}"] = round(us_row, 3)
+        res[name] = entry
+    print(json.dumps({"metric": "column transforms per arithmetic", "map": [N, N], "steps": args.steps,
+                      "solve": "headline (solver_params, solver_schedule, stop test on the refined s)",
+                      "results": res}))
     return 0
 
 
@@ -621,8 +679,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="headline", choices=["headline", "batch", "passes", "warm"])
+    ap.add_argument("--workload", default="headline", choices=["headline", "batch", "passes", "warm", "precision"])
     ap.add_argument("--size", type=int, default=N, help="map side for --workload passes")
+    ap.add_argument("--dft-precision", type=int, default=0, choices=[0, 1, 2],
+                    help="radix-16 stages of the column transforms for --workload passes: 0 FP32, "
+                         "1 split TF32 tensor cores, 2 TF32 tensor cores")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -632,6 +693,8 @@ def main():
         return run_passes(args)
     if args.workload == "warm":
         return run_warm(args)
+    if args.workload == "precision":
+        return run_precision(args)
     return run_gpu(args)
 
 

@@ -167,6 +167,18 @@ typedef struct {
  *  check_every     residual checkpoints between host polls of the done flag
  *                  (latency of the stop test versus host round trips);
  *                  default 8.
+ *  dft_precision   arithmetic of the radix-16 stages of the column transforms
+ *                  in the iteration's column pass and in wf_fft2: 0 (default)
+ *                  FP32 on the CUDA cores; 1 on the tensor cores as DFT
+ *                  matrix products with both factors split into two TF32
+ *                  parts (hi*hi + hi*lo + lo*hi, FP32 accumulation: about
+ *                  FP32 accuracy); 2 one TF32 product (relative error about
+ *                  2^-11 per stage).  The residual, the stop test and the
+ *                  defect corrections keep FP32 transforms and FP64 sums, so
+ *                  they judge a solve made with either.  Nonzero values need
+ *                  ny in {512, 1024, 2048, 4096} and merge_2df = 1
+ *                  (WF_EUNSUPPORTED otherwise); the column shape is then the
+ *                  16-value one.
  */
 typedef struct {
   double theta[3];
@@ -184,6 +196,7 @@ typedef struct {
   int refine_lam1_iters;
   int stall_checks;
   int autotune;
+  int dft_precision;
 } wf_params;
 
 /* Results of a solve. */
@@ -305,6 +318,7 @@ WF_API int wf_solve(wf_plan_t plan, const float* d, const float* pixel_var,
  *   rows_only = 1: only the row-wise transform (the stripe basis): in the
  *                same layout, column 0 holds (X[y][0], X[y][nx/2]) as a
  *                real pair per row.
+ * The column transforms follow the plan's dft_precision (wf_params).
  */
 WF_API int wf_fft2(wf_plan_t plan, const float* in, float* out, int inverse,
             int rows_only);

@@ -204,8 +204,11 @@ int wf::check_plan_args(int ny, int nx, unsigned parts, const wf_params* p) {
     return WF_EINVAL;
   if (!(prm.tol_u_scale > 0.0) || (prm.merge_2df != 0 && prm.merge_2df != 1)) return WF_EINVAL;
   if (prm.refine < 0 || prm.refine > 8 || !(prm.refine_tol_scale >= 1.0) || prm.refine_max_iters < 0 ||
-      prm.refine_lam1_iters < 0 || prm.stall_checks < 0 || prm.autotune < 0 || prm.autotune > 2)
+      prm.refine_lam1_iters < 0 || prm.stall_checks < 0 || prm.autotune < 0 || prm.autotune > 2 ||
+      prm.dft_precision < 0 || prm.dft_precision > 2)
     return WF_EINVAL;
+  // tensor-core radix-16 stages: 16-value column shapes, merged 2DF block
+  if (prm.dft_precision != 0 && (!col_tc_supported(ny) || prm.merge_2df != 1)) return WF_EUNSUPPORTED;
   return WF_OK;
 }
 
@@ -343,7 +346,8 @@ static RowArgs row_args(wf_plan_s* P) {
 
 static ColArgs col_args(wf_plan_s* P, int parity) {
   ColArgs a{};
-  a.variant = P->col_variant;
+  a.prec = P->p.dft_precision;
+  a.variant = a.prec ? 0 : P->col_variant;  // the tensor-core stages use the 16-value shape
   a.ny = P->ny;
   a.nx = P->nx;
   a.has_rf = P->has_rf;
@@ -463,7 +467,7 @@ static int finish_status(unsigned err) {
 
 namespace {
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int, unsigned, int>, std::pair<int, int>> g_tune;
+std::map<std::tuple<int, int, int, unsigned, int, int>, std::pair<int, int>> g_tune;
 }  // namespace
 
 // mean time of n launches of one pass with shape `variant`, in microseconds
@@ -497,7 +501,8 @@ static int time_pass(wf_plan_s* P, int which, int variant, int n, cudaEvent_t e0
 static int autotune(wf_plan_s* P) {
   int dev = 0;
   CK(cudaGetDevice(&dev));
-  const auto key = std::make_tuple(dev, P->ny, P->nx, P->parts, (int)P->merge);
+  const int prec = P->p.dft_precision;
+  const auto key = std::make_tuple(dev, P->ny, P->nx, P->parts, (int)P->merge, prec);
   // held while timing: plans of one shape on other threads wait for the
   // answer instead of timing concurrently and possibly choosing differently
   std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -509,7 +514,7 @@ static int autotune(wf_plan_s* P) {
     return WF_OK;
   }
   const bool two_rows = row_pass_e(P->M, 0) != row_pass_e(P->M, 1);
-  const bool two_cols = col_pass_e(P->ny, 0) != col_pass_e(P->ny, 1);
+  const bool two_cols = prec == 0 && col_pass_e(P->ny, 0) != col_pass_e(P->ny, 1);
   int rv = 0, cv = 0;
   if (two_rows || two_cols) {
     const int n = (int)std::min<size_t>(200, std::max<size_t>(8, (size_t)20000000 / ((size_t)P->ny * P->nx)));
@@ -1041,7 +1046,7 @@ int wf_fft2(wf_plan_t P, const float* in, float* out, int inverse, int rows_only
     if (!rows_only) {
       ca.in = P->r_g;
       ca.out = (float2*)dout;
-      CKI(launch_col(COL_FWD, ca, P->stream));
+      CKI(ca.prec ? launch_col_dft_tc(0, ca, P->stream) : launch_col(COL_FWD, ca, P->stream));
       P->launches += 1;
     }
   } else {
@@ -1049,7 +1054,7 @@ int wf_fft2(wf_plan_t P, const float* in, float* out, int inverse, int rows_only
     if (!rows_only) {
       ca.in = rin;
       ca.out = P->r_g;
-      CKI(launch_col(COL_INV, ca, P->stream));
+      CKI(ca.prec ? launch_col_dft_tc(1, ca, P->stream) : launch_col(COL_INV, ca, P->stream));
       P->launches += 1;
       rin = P->r_g;
     }
@@ -1068,7 +1073,7 @@ long long wf_launch_count(wf_plan_t P) { return P ? P->launches : -1; }
 int wf_plan_shapes(wf_plan_t P, int* row_values, int* col_values) {
   if (!P) return WF_EINVAL;
   if (row_values) *row_values = row_pass_e(P->M, P->row_variant);
-  if (col_values) *col_values = col_pass_e(P->ny, P->col_variant);
+  if (col_values) *col_values = col_pass_e(P->ny, P->p.dft_precision ? 0 : P->col_variant);
   return WF_OK;
 }
 

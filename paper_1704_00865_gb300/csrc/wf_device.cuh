@@ -193,16 +193,169 @@ __device__ __forceinline__ void fft_sync() {
   else __syncthreads();
 }
 
+// 32-bit shared-memory address of a generic pointer into shared memory
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// ---------------------------------------------------------------- tensor-core radix-16
+// A radix-16 stage as a matrix product on the tensor cores (DFT as GEMM): for
+// the 32 length-16 DFTs held by one warp (one per lane, B = E/R = 1),
+// Y[k][n] = sum_r W16^{kr} U[r][n], with complex values split into real
+// products Yr = Fr Ur - Fi Ui, Yi = Fr Ui + Fi Ur, each an m16n8k8 TF32 MMA
+// per 8 lanes (n) and 8 inputs (r), FP32 accumulation.  PREC = 1 splits both
+// factors as x = hi + lo with hi = TF32(x), lo = TF32(x - hi) and sums
+// hi*hi + hi*lo + lo*hi (about FP32 accuracy); PREC = 2 takes hi*hi alone
+// (TF32 accuracy, 2^-11 relative per product).
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+template <int PREC>
+__device__ __forceinline__ void tf32_split(float x, uint32_t& hi, uint32_t& lo) {
+  hi = to_tf32(x);
+  if constexpr (PREC == 1) lo = to_tf32(x - __uint_as_float(hi));
+  else lo = 0u;
+}
+// d += a b for one m16n8k8 tile: a 16 x 8 (row), b 8 x 8 (column), d 16 x 8.
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+// d += a b with the split factors (PREC = 1: three products, small ones first)
+template <int PREC>
+__device__ __forceinline__ void mma_split(float (&d)[4], const uint32_t (&ah)[4], const uint32_t (&al)[4],
+                                          uint32_t bh0, uint32_t bh1, uint32_t bl0, uint32_t bl1) {
+  if constexpr (PREC == 1) {
+    mma_tf32(d, al, bh0, bh1);
+    mma_tf32(d, ah, bl0, bl1);
+  }
+  mma_tf32(d, ah, bh0, bh1);
+}
+__device__ __forceinline__ float2 lds_f2(uint32_t addr) {
+  float2 v;
+  asm volatile("ld.shared.v2.f32 {%0,%1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr) : "memory");
+  return v;
+}
+__device__ __forceinline__ void sts_f2(uint32_t addr, float2 v) {
+  asm volatile("st.shared.v2.f32 [%0], {%1,%2};" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
+}
+
+// The stage with sub-transform length NS of a length-L transform whose
+// threads hold E = 16 values each.  Each lane's own inputs (twiddled as in the
+// FP32 stage) are staged at 16 t + r of its transform's buffer; the lanes read
+// the operand fragments of the warp's 32 transforms from there (addresses and
+// t of the other lanes by shuffles, so any lane-to-transform layout works);
+// after a block barrier the outputs go to their autosort positions.  Every
+// thread of the block calls it; sb is free on entry.
+template <int L, int NS, bool INV, bool TWS, int PREC>
+__device__ __forceinline__ void tc_radix16_stage(float2 (&v)[16], float2* sb, int t,
+                                                 const float2* __restrict__ twtab, int twstride) {
+  const int lane = threadIdx.x & 31, gid = lane >> 2, tig = lane & 3;
+  const uint32_t mine = smem_u32(sb);
+  if constexpr (NS > 1) {
+    const int jm = t % NS;
+    const int step = jm * (L / (NS * 16)) * twstride;
+    float2 w1 = tw_dir<INV>(tw_load<TWS>(twtab, step));
+    float2 wr = w1;
+#pragma unroll
+    for (int r = 1; r < 16; ++r) {
+      if ((r & 3) == 0) wr = tw_dir<INV>(tw_load<TWS>(twtab, step * r));
+      v[r] = cmul(v[r], wr);
+      wr = cmul(wr, w1);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 16; ++r) sb[spad(16 * t + r)] = v[r];
+  __syncwarp();
+  float yr[4][4], yi[4][4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) yr[q][i] = yi[q][i] = 0.f;
+#pragma unroll
+  for (int ks = 0; ks < 2; ++ks) {
+    // A fragments of F = W16^{kr}: a_i at row k = gid + 8 (i & 1), column
+    // r = tig + 4 (i >> 1) of this k-step (inputs 8 ks .. 8 ks + 7)
+    uint32_t frh[4], frl[4], fih[4], fil[4], nfih[4], nfil[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int k = gid + 8 * (i & 1), r = tig + 4 * (i >> 1) + 8 * ks;
+      const float2 w = tw_dir<INV>(tw_load<TWS>(twtab, ((k * r) & 15) * (L / 16) * twstride));
+      tf32_split<PREC>(w.x, frh[i], frl[i]);
+      tf32_split<PREC>(w.y, fih[i], fil[i]);
+      nfih[i] = fih[i] ^ 0x80000000u;
+      nfil[i] = fil[i] ^ 0x80000000u;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      // B fragments: b0 = U[r = 8 ks + tig][n], b1 = U[r + 4][n], n = gid + 8 q
+      const int n = gid + 8 * q;
+      const int tn = __shfl_sync(0xffffffffu, t, n);
+      const uint32_t an = __shfl_sync(0xffffffffu, mine, n);
+      const int r0 = 8 * ks + tig;
+      const float2 u0 = lds_f2(an + 8u * (uint32_t)spad(16 * tn + r0));
+      const float2 u1 = lds_f2(an + 8u * (uint32_t)spad(16 * tn + r0 + 4));
+      uint32_t rh0, rl0, rh1, rl1, ih0, il0, ih1, il1;
+      tf32_split<PREC>(u0.x, rh0, rl0);
+      tf32_split<PREC>(u1.x, rh1, rl1);
+      tf32_split<PREC>(u0.y, ih0, il0);
+      tf32_split<PREC>(u1.y, ih1, il1);
+      mma_split<PREC>(yr[q], frh, frl, rh0, rh1, rl0, rl1);    // + Fr Ur
+      mma_split<PREC>(yr[q], nfih, nfil, ih0, ih1, il0, il1);  // - Fi Ui
+      mma_split<PREC>(yi[q], frh, frl, ih0, ih1, il0, il1);    // + Fr Ui
+      mma_split<PREC>(yi[q], fih, fil, rh0, rh1, rl0, rl1);    // + Fi Ur
+    }
+  }
+  __syncthreads();  // every warp has read its staged inputs
+  // D fragments: d_i at row k = gid + 8 (i >> 1), column n = 2 tig + (i & 1)
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int n = 2 * tig + h + 8 * q;
+      const int tn = __shfl_sync(0xffffffffu, t, n);
+      const uint32_t an = __shfl_sync(0xffffffffu, mine, n);
+      const int jm = tn % NS;
+      const int base = (tn - jm) * 16 + jm;
+      sts_f2(an + 8u * (uint32_t)spad(base + gid * NS), make_float2(yr[q][h], yi[q][h]));
+      sts_f2(an + 8u * (uint32_t)spad(base + (gid + 8) * NS), make_float2(yr[q][2 + h], yi[q][2 + h]));
+    }
+  }
+}
+
 // One Stockham autosort stage (radix R, sub-transform length NS) of a
 // length-L complex DFT computed by TPF = L/E threads, E values per thread.
 // Inputs are the "natural" layout (thread t holds x[t + m*TPF], m =
 // b + r*(E/R)); outputs go to shared memory at their autosort positions, or,
 // for the last stage, back to the registers in the natural layout.
-// twtab holds exp(-2 pi i k / (L*twstride)), k < L*twstride.
-template <int L, int E, int NS, bool INV, bool WARP, bool TWS = false>
+// twtab holds exp(-2 pi i k / (L*twstride)), k < L*twstride.  PREC != 0 runs
+// the radix-16 stages of 16-value threads on the tensor cores (above).
+template <int L, int E, int NS, bool INV, bool WARP, bool TWS = false, int PREC = 0>
 struct FFTStages {
   static __device__ __forceinline__ void run(float2 (&v)[E], float2* sb, int t,
                                              const float2* __restrict__ twtab, int twstride) {
+    constexpr int R = StageRadix<L, E, NS>::value;
+    constexpr int TPF = L / E;
+    constexpr bool LAST = (NS * R == L);
+    constexpr bool TC = (PREC != 0 && R == 16 && E == 16 && !WARP);
+    if constexpr (TC) {
+      tc_radix16_stage<L, NS, INV, TWS, PREC>(v, sb, t, twtab, twstride);
+      fft_sync<WARP>();
+#pragma unroll
+      for (int m = 0; m < E; ++m) v[m] = sb[spad(t + m * TPF)];
+      fft_sync<WARP>();
+      if constexpr (!LAST) FFTStages<L, E, NS * R, INV, WARP, TWS, PREC>::run(v, sb, t, twtab, twstride);
+    } else {
+      stage_fp32(v, sb, t, twtab, twstride);
+    }
+  }
+
+  static __device__ __forceinline__ void stage_fp32(float2 (&v)[E], float2* sb, int t,
+                                                    const float2* __restrict__ twtab, int twstride) {
     constexpr int R = StageRadix<L, E, NS>::value;
     constexpr int TPF = L / E;
     constexpr int B = E / R;
@@ -242,7 +395,7 @@ struct FFTStages {
 #pragma unroll
       for (int m = 0; m < E; ++m) v[m] = sb[spad(t + m * TPF)];
       fft_sync<WARP>();
-      FFTStages<L, E, NS * R, INV, WARP, TWS>::run(v, sb, t, twtab, twstride);
+      FFTStages<L, E, NS * R, INV, WARP, TWS, PREC>::run(v, sb, t, twtab, twstride);
     }
   }
 };
@@ -250,10 +403,10 @@ struct FFTStages {
 // Full complex DFT of length L (no scaling).  Every thread of the block (or
 // of the warp, WARP = true) must call it; sb is this transform's own padded
 // shared buffer of SPad<L>::size values.
-template <int L, int E, bool INV, bool WARP = false, bool TWS = false>
+template <int L, int E, bool INV, bool WARP = false, bool TWS = false, int PREC = 0>
 __device__ __forceinline__ void fft_block(float2 (&v)[E], float2* sb, int t,
                                           const float2* __restrict__ twtab, int twstride) {
-  FFTStages<L, E, 1, INV, WARP, TWS>::run(v, sb, t, twtab, twstride);
+  FFTStages<L, E, 1, INV, WARP, TWS, PREC>::run(v, sb, t, twtab, twstride);
 }
 
 // W_N^k (N = 2M) for the k = t + m*(M/E) a thread handles in c2r_pre and
@@ -372,9 +525,6 @@ __device__ __forceinline__ void r2c_post(float2 (&v)[E], float2* sb, int t,
 // ---------------------------------------------------------------- TMA bulk copies
 // 1D bulk copies global -> shared (cp.async.bulk) completed on an mbarrier.
 // Addresses and sizes must be multiples of 16 bytes.
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }

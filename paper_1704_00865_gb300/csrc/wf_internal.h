@@ -128,6 +128,7 @@ struct ColArgs {
   const float2* src;          // 2D-Fourier source j^ (column-tiled) or nullptr
   float2* warm_copy;          // COL_WARM: tiled copy of the input (t_RF or t_PX)
   int variant;                // column pass shape (0 or 1), chosen by the autotuner
+  int prec;                   // radix-16 stages of the column pass: 0 FP32, 1 split TF32, 2 TF32
 };
 
 // launchers (return a cudaError_t as int)
@@ -137,6 +138,12 @@ int row_grid(int nx, int ny);  // CTAs of a row pass (size of partial-sum arrays
 bool size_supported(int n);
 // argument checks of wf_plan_create (host only; WF_OK or a WF_E* code)
 int check_plan_args(int ny, int nx, unsigned parts, const wf_params* p);
+// the column pass and the column transforms of wf_fft2 with tensor-core
+// radix-16 stages (a.prec = 1 or 2; column lengths 512 to 4096, merged 2DF
+// block); cudaErrorInvalidValue for other lengths or modes
+int launch_col_pass_tc(int L, int mode, const ColArgs& a, cudaStream_t s);
+int launch_col_dft_tc(int inverse, const ColArgs& a, cudaStream_t s);
+bool col_tc_supported(int L);
 // values per thread of the row / column pass shape `variant` for a length
 int row_pass_e(int M, int variant);
 int col_pass_e(int L, int variant);

@@ -44,7 +44,8 @@ class wf_params(C.Structure):
                 ("split_w", C.c_double), ("tol_u_scale", C.c_double), ("residual_every", C.c_int), ("max_iters", C.c_int),
                 ("check_every", C.c_int), ("merge_2df", C.c_int), ("refine", C.c_int),
                 ("refine_tol_scale", C.c_double), ("refine_max_iters", C.c_int),
-                ("refine_lam1_iters", C.c_int), ("stall_checks", C.c_int), ("autotune", C.c_int)]
+                ("refine_lam1_iters", C.c_int), ("stall_checks", C.c_int), ("autotune", C.c_int),
+                ("dft_precision", C.c_int)]
 
 
 class wf_stats(C.Structure):
@@ -179,8 +180,11 @@ def wf_params_default() -> wf_params:
 def make_params(theta=None, split_f=None, split_w=None, residual_every=None, max_iters=None,
                 check_every=None, merge_2df=None, tol_u_scale=None, split_fp=None,
                 refine=None, refine_tol_scale=None, refine_max_iters=None,
-                refine_lam1_iters=None, stall_checks=None, autotune=None) -> wf_params:
+                refine_lam1_iters=None, stall_checks=None, autotune=None,
+                dft_precision=None) -> wf_params:
     p = wf_params_default()
+    if dft_precision is not None:
+        p.dft_precision = int(dft_precision)
     if autotune is not None:
         p.autotune = int(autotune)
     if stall_checks is not None:

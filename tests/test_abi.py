@@ -51,6 +51,7 @@ def test_host_only_entry_points(lib):
     assert p.residual_every == 10 and p.check_every == 8
     assert p.merge_2df == 1 and p.tol_u_scale == 1.0 and p.refine == 0 and p.refine_tol_scale == 100.0
     assert p.autotune == 1 and p.stall_checks == 0 and p.refine_max_iters == 0
+    assert p.dft_precision == 0
     assert lib.wf_plan_shapes(None, None, None) == wf.WF_EINVAL
 
 
@@ -72,10 +73,23 @@ def test_plan_create_rejects_bad_params(lib):
     for kw in (dict(theta=(0.9, 1.5, 1.0)), dict(split_f=0.5, split_fp=0.5, merge_2df=0), dict(split_f=1.01, split_fp=0.0), dict(split_f=0.6, split_fp=0.6),
                dict(residual_every=0), dict(tol_u_scale=0.0), dict(refine=-1), dict(refine=9),
                dict(refine_max_iters=-1), dict(refine_lam1_iters=-1), dict(stall_checks=-1),
-               dict(autotune=3)):
+               dict(autotune=3), dict(dft_precision=-1), dict(dft_precision=3)):
         p = wf.make_params(**kw)
         h = C.c_void_p()
         assert lib.wf_plan_create(C.byref(h), 64, 64, 7, C.byref(p), None) == wf.WF_EINVAL
+
+
+@pytest.mark.parametrize("ny,kw", [
+    (256, dict(dft_precision=1)),                 # no 16-value column shape at 256
+    (1536, dict(dft_precision=2)),                # 3 * 2^k columns
+    (1024, dict(dft_precision=1, merge_2df=0, split_fp=0.3)),  # plain sweep (stored t_2DF)
+])
+def test_tensor_core_stages_reject_unsupported_plans(lib, ny, kw):
+    from paper_1704_00865_gb300 import wf
+    p = wf.make_params(**kw)
+    h = C.c_void_p()
+    assert lib.wf_plan_create(C.byref(h), ny, 64, 7, C.byref(p), None) == wf.WF_EUNSUPPORTED
+    assert h.value is None
 
 
 def test_product_path_never_imports_the_oracle():
@@ -92,7 +106,7 @@ def test_schedule_struct_layout_matches_header(lib):
     from paper_1704_00865_gb300 import wf
     # int, ptr, ptr, int, 4 doubles on LP64
     assert C.sizeof(wf.wf_schedule) == 4 + 4 + 8 + 8 + 4 + 4 + 32
-    assert C.sizeof(wf.wf_params) == 24 + 24 + 8 + 16 + 8 + 8 + 8 + 8
+    assert C.sizeof(wf.wf_params) == 24 + 24 + 8 + 16 + 8 + 8 + 8 + 8 + 8
     assert C.sizeof(wf.wf_stats) == 8 + 8 * 3 + 24 + 8
 
 
