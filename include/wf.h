@@ -156,13 +156,21 @@ typedef struct {
  *                  map shape for the process (see wf_plan_shapes); 0: the
  *                  first shapes; 2: the second shapes, untimed.  The shape
  *                  changes only the rounding order.
+ *  refine_extra    further corrections after the refine ones, each run only
+ *                  while the refined s fails the stop test (tol > 0): a
+ *                  harder map gets the sweeps it needs without raising the
+ *                  budget of every map; default 0, at most 8.
  *  refine_lam1_iters with a cap and a fixed schedule, each correction runs
  *                  the schedule's levels (lambda > 1) for at most
  *                  refine_max_iters - refine_lam1_iters sweeps and then
  *                  lambda = 1 to the cap, so that it ends on the unbiased
  *                  fixed point; default 0.
  *  residual_every  R: the residual and the lambda rule run every R
- *                  iterations; default 10.
+ *                  iterations; default 10.  With a fixed schedule the
+ *                  residual is evaluated only where something uses it: at
+ *                  lambda = 1 (stop and stall tests) and at the checkpoint
+ *                  that reaches max_iters (the values reported); the other
+ *                  checkpoints only advance the schedule.
  *  max_iters       default 200000.
  *  check_every     residual checkpoints between host polls of the done flag
  *                  (latency of the stop test versus host round trips);
@@ -197,6 +205,7 @@ typedef struct {
   int stall_checks;
   int autotune;
   int dft_precision;
+  int refine_extra;
 } wf_params;
 
 /* Results of a solve. */

@@ -205,6 +205,7 @@ int wf::check_plan_args(int ny, int nx, unsigned parts, const wf_params* p) {
   if (!(prm.tol_u_scale > 0.0) || (prm.merge_2df != 0 && prm.merge_2df != 1)) return WF_EINVAL;
   if (prm.refine < 0 || prm.refine > 8 || !(prm.refine_tol_scale >= 1.0) || prm.refine_max_iters < 0 ||
       prm.refine_lam1_iters < 0 || prm.stall_checks < 0 || prm.autotune < 0 || prm.autotune > 2 ||
+      prm.refine_extra < 0 || prm.refine_extra > 8 ||
       prm.dft_precision < 0 || prm.dft_precision > 2)
     return WF_EINVAL;
   // tensor-core radix-16 stages: 16-value column shapes, merged 2DF block
@@ -395,9 +396,11 @@ static int enqueue_iteration(wf_plan_s* P, int parity) {
 static int enqueue_residual(wf_plan_s* P, int parity, int check_done) {
   ColArgs ca = col_args(P, parity);
   ca.check_done = check_done;
+  ca.skip_ok = check_done;  // iteration checkpoints only
   CKI(launch_col(COL_RESID_A, ca, P->stream));
   RowArgs ra = row_args(P);
   ra.check_done = check_done;
+  ra.skip_ok = check_done;
   ra.part0 = P->part;
   ra.part1 = P->part + P->nrow;
   CKI(launch_row(ROW_RESID_B, ra, P->stream));
@@ -661,6 +664,7 @@ static int wf_run_on(wf_plan_t P, const wf_schedule* sch, double tol, wf_stats* 
     CK(cudaMemcpyAsync(P->lam_sched, L.data(), L.size() * sizeof(double), cudaMemcpyHostToDevice, P->stream));
     CK(cudaMemcpyAsync(P->it_sched, I.data(), I.size() * sizeof(int), cudaMemcpyHostToDevice, P->stream));
     c.mode = 0;
+    c.skip_fixed = 1;
     c.nlevels = (int)L.size();
     lam0 = L[0];
   } else if (sch->mode == WF_SCHED_ADAPTIVE) {
@@ -711,6 +715,7 @@ static int wf_run_on(wf_plan_t P, const wf_schedule* sch, double tol, wf_stats* 
   const long long par = it0 & 1, src = P->has_src ? 1 : 0;
   put(&c.tol, 8); put(&c.tol_u, 8); put(&c.ratio, 8); put(&c.expo, 8); put(&c.snap, 8);
   put(&c.mode, 4); put(&c.nlevels, 4); put(&c.R, 4); put(&c.max_iters, 4); put(&c.count_iters, 4);
+  put(&c.skip_fixed, 4);
   put(&par, 8); put(&src, 8);
   const bool use_graph = (per_chunk % 2 == 0);
   bool first = true;
@@ -926,9 +931,11 @@ static int solve_impl(wf_plan_t P, const float* d, const float* pixel_var, const
     csched.iters = citers.data();
     csched.nlevels = (int)clam.size();
   }
-  for (int r = 0; r < P->p.refine; ++r) {
+  // one correction: s_acc <- s_acc - WF(residual of s_acc)
+  auto correct = [&]() -> int {
     // residual of the accumulated s: Delta d_u (data) and (S^-1 s)_m (source)
-    if ((rc = enqueue_resid_map(P, P->s_acc, P->rho, P->jmap))) return rc;
+    int rc2 = enqueue_resid_map(P, P->s_acc, P->rho, P->jmap);
+    if (rc2) return rc2;
     CKI(launch_pack_data(P->dn, P->dn_orig, P->rho, npx / 2, P->part + 3 * P->nrow, P->st, P->stream));
     P->launches += 2;
     if (with_src) {
@@ -955,28 +962,43 @@ static int solve_impl(wf_plan_t P, const float* d, const float* pixel_var, const
     if (P->p.refine_max_iters > 0) P->p.max_iters = P->p.refine_max_iters;
     int sr_status = wf_run(P, &csched, tol * P->p.refine_tol_scale, &sr);
     P->p.max_iters = main_cap;
-    if (finished(sr_status)) rc = wf_get_field(P, WF_FIELD_S, P->s_corr);
+    if (finished(sr_status)) rc2 = wf_get_field(P, WF_FIELD_S, P->s_corr);
     P->has_src = false;
     if (!finished(sr_status)) return sr_status;
-    if (rc) return rc;
+    if (rc2) return rc2;
     // a correction that runs to refine_max_iters has done what was asked
     if (sr_status != WF_OK && P->p.refine_max_iters == 0 && status == WF_OK) status = sr_status;
     tot.iters += sr.iters;
     tot.checkpoints += sr.checkpoints;
     CKI(launch_sub(P->s_acc, P->s_corr, npx, P->stream));
     P->launches += 1;
+    return WF_OK;
+  };
+  // residual of the refined s against the original problem, into h_st
+  auto judge = [&]() -> int {
+    int rc2 = enqueue_resid_map(P, P->s_acc, P->rho, nullptr);
+    if (rc2) return rc2;
+    CK(cudaMemcpyAsync(&P->st->du2, &du2, sizeof(double), cudaMemcpyHostToDevice, P->stream));
+    CtrlArgs c = ctrl_args(P);
+    c.count_iters = 0;
+    CKI(launch_ctrl(c, P->stream));
+    P->launches += 1;
+    CK(cudaMemcpyAsync(P->h_st, P->st, sizeof(WfState), cudaMemcpyDeviceToHost, P->stream));
+    CK(cudaStreamSynchronize(P->stream));
+    return WF_OK;
+  };
+  auto passes = [&]() { return P->h_st->rel_u <= tol * P->p.tol_u_scale && P->h_st->rel_m <= tol; };
+  for (int r = 0; r < P->p.refine; ++r)
+    if ((rc = correct())) return rc;
+  if ((rc = judge())) return rc;
+  // further corrections only while the refined s fails the stop test
+  for (int r = 0; tol > 0 && r < P->p.refine_extra && !passes(); ++r) {
+    if ((rc = correct())) return rc;
+    if ((rc = judge())) return rc;
   }
-  // residual of the refined s against the original problem
-  if ((rc = enqueue_resid_map(P, P->s_acc, P->rho, nullptr))) return rc;
-  CK(cudaMemcpyAsync(&P->st->du2, &du2, sizeof(double), cudaMemcpyHostToDevice, P->stream));
-  CtrlArgs c = ctrl_args(P);
-  c.count_iters = 0;
-  CKI(launch_ctrl(c, P->stream));
-  P->launches += 1;
   const bool dev = is_device_ptr(s_out);
   CK(cudaMemcpyAsync(s_out, P->s_acc, npx * sizeof(float), dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                      P->stream));
-  CK(cudaMemcpyAsync(P->h_st, P->st, sizeof(WfState), cudaMemcpyDeviceToHost, P->stream));
   CK(cudaStreamSynchronize(P->stream));
   // the plan now holds the last correction problem, not the caller's
   P->loaded = false;
@@ -984,8 +1006,7 @@ static int solve_impl(wf_plan_t P, const float* d, const float* pixel_var, const
   tot.rel_rho_m = P->h_st->rel_m;
   if (tol > 0) {
     // the refined s is judged by the stop test itself
-    const bool pass = tot.rel_rho_u <= tol * P->p.tol_u_scale && tot.rel_rho_m <= tol;
-    status = pass ? WF_OK : (status == WF_OK ? WF_ENOCONV : status);
+    status = passes() ? WF_OK : (status == WF_OK ? WF_ENOCONV : status);
   }
   tot.status = status;
   if (st) *st = tot;

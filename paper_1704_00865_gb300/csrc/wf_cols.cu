@@ -47,7 +47,8 @@ col_kernel(ColArgs a) {
   const int colv = valid ? col : 0;
   float2* sb = sbuf[c];
 
-  if (a.check_done && a.st->done) return;  // uniform: set only between launches
+  // uniform: both flags are set only between launches
+  if ((a.check_done && a.st->done) || (a.skip_ok && a.st->skip_resid)) return;
 
   auto at = [&](int k) -> size_t { return (size_t)k * ncols + colv; };       // row-major
   auto att = [&](int k) -> size_t { return tidx(k, colv, a.ny); };           // column-tiled

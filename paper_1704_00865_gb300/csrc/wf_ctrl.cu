@@ -224,6 +224,7 @@ __global__ void set_lambda_kernel(WfState* st, double lam, int reset) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   st->lam = lam;
   set_T(st);
+  st->skip_resid = 0;
   if (reset) {
     st->done = 0;
     st->status = 0;
@@ -310,26 +311,34 @@ __global__ void __launch_bounds__(CTRL_THREADS) ctrl_kernel(CtrlArgs a) {
   pdl_trigger();
   pdl_wait();
   if (a.count_iters && st->done) return;
+  // the residual kernels of this checkpoint returned at once (uniform: the
+  // flag changes below only after every thread has read it)
+  const bool skipped = a.count_iters && st->skip_resid;
+  __syncthreads();
   double gm2 = 0.0, g2 = 0.0, r2 = 0.0;
-  for (int i = threadIdx.x; i < a.nrow; i += blockDim.x) {
-    gm2 += a.part_g[i];
-    g2 += a.part_g2[i];
-    r2 += a.part_rho[i];
+  if (!skipped) {
+    for (int i = threadIdx.x; i < a.nrow; i += blockDim.x) {
+      gm2 += a.part_g[i];
+      g2 += a.part_g2[i];
+      r2 += a.part_rho[i];
+    }
+    gm2 = block_add<CTRL_THREADS>(gm2, red);
+    g2 = block_add<CTRL_THREADS>(g2, red);
+    r2 = block_add<CTRL_THREADS>(r2, red);
   }
-  gm2 = block_add<CTRL_THREADS>(gm2, red);
-  g2 = block_add<CTRL_THREADS>(g2, red);
-  r2 = block_add<CTRL_THREADS>(r2, red);
   if (threadIdx.x != 0) return;
-  st->gm2 = gm2;
-  st->g2 = g2;
-  st->rho2 = r2;
-  st->rel_u = st->du2 > 0 ? sqrt(r2 / st->du2) : 0.0;
-  st->rel_m = g2 > 0 ? sqrt(gm2 / g2) : 0.0;
+  if (!skipped) {
+    st->gm2 = gm2;
+    st->g2 = g2;
+    st->rho2 = r2;
+    st->rel_u = st->du2 > 0 ? sqrt(r2 / st->du2) : 0.0;
+    st->rel_m = g2 > 0 ? sqrt(gm2 / g2) : 0.0;
+  }
   if (!a.count_iters) return;  // residual only
   st->iter += a.R;
   st->in_level += a.R;
   st->checkpoints += 1;
-  if (a.tol > 0 && st->lam == 1.0 && st->rel_u <= a.tol_u && st->rel_m <= a.tol) {
+  if (!skipped && a.tol > 0 && st->lam == 1.0 && st->rel_u <= a.tol_u && st->rel_m <= a.tol) {
     st->done = 1;
     st->status = 0;
     return;
@@ -360,6 +369,10 @@ __global__ void __launch_bounds__(CTRL_THREADS) ctrl_kernel(CtrlArgs a) {
       st->stall_n = 0;
       set_T(st);
     }
+    // a fixed schedule uses the residual only at lambda = 1 (stop and stall
+    // tests) and at the checkpoint that ends the run (the reported values):
+    // the next checkpoint skips it otherwise
+    st->skip_resid = (a.skip_fixed && st->lam > 1.0 && st->iter + a.R < a.max_iters) ? 1 : 0;
   } else if (st->lam > 1.0) {
     // Sec. 3.3: lower lambda once Delta d^T Delta d changes by less than
     // `ratio` per iteration

@@ -596,7 +596,8 @@ struct WfState {
   int checkpoints;
   int level, in_level;
   int stall_n;        // checkpoints at lambda = 1 without a 1% drop of rho2
-  int pad_;
+  int skip_resid;     // 1: the next checkpoint's residual is not needed (fixed
+                      // schedule above lambda = 1, not the last checkpoint)
   double stall_ref;   // rho2 those checkpoints are measured against (<= 0: none)
 };
 

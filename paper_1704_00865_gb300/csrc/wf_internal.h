@@ -85,6 +85,7 @@ struct RowArgs {
   int ny, nx;
   int has_rf;                 // stripe part present
   int check_done;             // return at once when the solver is done
+  int skip_ok;                // residual kernels: return at once when st->skip_resid
   const float4* dn;           // [ny][nx/2] pixel pairs (d0, nb0, d1, nb1); nb < 0 = masked
   float2* f_d1;               // RF fields [ny][nx/2]
   float2* f_t1;
@@ -113,6 +114,7 @@ struct ColArgs {
   int has_rf, has_f;
   int merge;                  // 2DF block updated jointly (no stored t_2DF)
   int check_done;             // return at once when the solver is done
+  int skip_ok;                // residual kernels: return at once when st->skip_resid
   int parity;                 // slot of T0s holding the stored t_2DF's T_0
   const float2* f_y;          // data-side messenger in RF (t_RF or t_PX)
   float2* f_x;                // output in RF (d_2DF or s)
@@ -188,6 +190,7 @@ struct CtrlArgs {
   int nlevels;
   double ratio, expo, snap;
   int count_iters;            // add R to iter (0 for a residual-only call)
+  int skip_fixed;             // fixed schedule: skip residuals nothing uses (st->skip_resid)
   int stall;                  // stop after this many checkpoints at lambda = 1
                               // without a 1% drop of ||Delta d_u||^2 (0: never)
 };

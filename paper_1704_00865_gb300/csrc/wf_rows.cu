@@ -63,7 +63,8 @@ row_kernel(RowArgs a) {
   const size_t row0 = (size_t)(valid ? y : 0) * M;
   float2* sb = sbuf[g];
 
-  if (a.check_done && a.st->done) return;  // uniform: set only between launches
+  // uniform: both flags are set only between launches
+  if ((a.check_done && a.st->done) || (a.skip_ok && a.st->skip_resid)) return;
 
   float2 v[E];
 

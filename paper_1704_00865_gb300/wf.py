@@ -45,7 +45,7 @@ class wf_params(C.Structure):
                 ("check_every", C.c_int), ("merge_2df", C.c_int), ("refine", C.c_int),
                 ("refine_tol_scale", C.c_double), ("refine_max_iters", C.c_int),
                 ("refine_lam1_iters", C.c_int), ("stall_checks", C.c_int), ("autotune", C.c_int),
-                ("dft_precision", C.c_int)]
+                ("dft_precision", C.c_int), ("refine_extra", C.c_int)]
 
 
 class wf_stats(C.Structure):
@@ -181,8 +181,10 @@ def make_params(theta=None, split_f=None, split_w=None, residual_every=None, max
                 check_every=None, merge_2df=None, tol_u_scale=None, split_fp=None,
                 refine=None, refine_tol_scale=None, refine_max_iters=None,
                 refine_lam1_iters=None, stall_checks=None, autotune=None,
-                dft_precision=None) -> wf_params:
+                dft_precision=None, refine_extra=None) -> wf_params:
     p = wf_params_default()
+    if refine_extra is not None:
+        p.refine_extra = int(refine_extra)
     if dft_precision is not None:
         p.dft_precision = int(dft_precision)
     if autotune is not None:

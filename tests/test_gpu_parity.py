@@ -310,3 +310,33 @@ def test_inverse_noise_mode(wf, shape, kw):
     assert rel(w, O.inverse_noise_dense(prob)) < 3e-3
     m = prob.mask.astype(bool)
     assert np.linalg.norm(w[m]) < 1e-3 * np.linalg.norm(w)   # masked pixels carry no weight
+
+
+def test_extra_corrections_run_only_while_the_stop_test_fails(wf):
+    # a budget too small for the stop test: refine_extra adds corrections of
+    # refine_max_iters sweeps one at a time and stops at the first refined s
+    # that passes; a map that already passes gets none
+    prob = synth.make_problem(32, 64, 61, mask_frac=0.08, k_knee=4.0, k_knee_x=4.0)
+    sched = wf.make_schedule("fixed", [10.0], [30])
+    # (50 sweeps measured: 9 corrections take the error from 3.3e-2 to 5.5e-5)
+    small = dict(residual_every=10, max_iters=50, refine_max_iters=100, refine_lam1_iters=30, tol_u_scale=20.0)
+    s0, st0 = _solve_refined(wf, prob, sched, 1e-5, 1, **small)
+    assert st0["status"] == wf.WF_ENOCONV, st0
+    s8, st8 = _solve_refined(wf, prob, sched, 1e-5, 1, refine_extra=8, **small)
+    k = (st8["iters"] - st0["iters"]) // 100
+    assert k >= 1 and st8["iters"] == st0["iters"] + 100 * k, (st0, st8)
+    assert st8["status"] == 0 or k == 8, st8
+    ref = O.dense_wf(prob)
+    print(f"32x64, 100-sweep corrections: {k} extra, status {st8['status']}, "
+          f"rel L2 vs dense {rel(s0, ref):.2e} -> {rel(s8, ref):.2e}")
+    assert rel(s8, ref) < rel(s0, ref)
+    if st8["status"] == 0 and k > 1:
+        # one extra correction fewer still fails: the loop stopped at the first pass
+        _, stk = _solve_refined(wf, prob, sched, 1e-5, 1, refine_extra=k - 1, **small)
+        assert stk["status"] == wf.WF_ENOCONV and stk["iters"] == st0["iters"] + 100 * (k - 1), stk
+    # a generous budget passes without extras: bit-identical with and without
+    big = dict(residual_every=10, max_iters=20000, refine_max_iters=2000, refine_lam1_iters=500, tol_u_scale=20.0)
+    sched2 = wf.make_schedule("fixed", O.cooling_levels(1e2, 5), [20] * 5)
+    a, sa = _solve_refined(wf, prob, sched2, 1e-5, 1, **big)
+    b, sb = _solve_refined(wf, prob, sched2, 1e-5, 1, refine_extra=8, **big)
+    assert sa["status"] == 0 and sb["iters"] == sa["iters"] and np.array_equal(a, b), (sa, sb)
