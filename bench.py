@@ -606,7 +606,8 @@ def run_passes(args):
     p = synth.make_problem(n, n, SEED + n)
     dev = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).cuda()
     plan = wf.Plan(n, n, wf.parts_of(p), wf.make_params(merge_2df=1, split_f=SPLIT_F, split_fp=SPLIT_FP,
-                                                         dft_precision=args.dft_precision))
+                                                         dft_precision=args.dft_precision,
+                                                         autotune=args.autotune))
     plan.set_problem(*(dev(a) for a in (p.d, p.pixel_var, p.mask, p.C, p.P1f, p.Pst, p.stripe_amp2)))
     plan.iterate(1.0, 20)
     reps = max(20, int(2e8 / (n * n)))
@@ -691,6 +692,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="headline", choices=["headline", "batch", "passes", "warm", "precision"])
     ap.add_argument("--size", type=int, default=N, help="map side for --workload passes")
+    ap.add_argument("--autotune", type=int, default=1, choices=[0, 1, 2],
+                    help="pass shapes for --workload passes: 1 timed (default), 0 first, 2 second shapes")
     ap.add_argument("--dft-precision", type=int, default=0, choices=[0, 1, 2],
                     help="radix-16 stages of the column transforms for --workload passes: 0 FP32, "
                          "1 split TF32 tensor cores, 2 TF32 tensor cores")
