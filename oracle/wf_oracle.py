@@ -76,7 +76,7 @@ __all__ = [
     "cooling_levels", "apply_N", "apply_Sinv", "residual_terms", "pcg",
     "literal_residual", "pcg_wf", "chi2", "rel_l2", "DEFAULT_THETA",
     "ADAPTIVE_DEFAULT", "DEFAULT_SPLIT_F", "rel_terms", "to_basis", "from_basis",
-    "inverse_noise_dense",
+    "inverse_noise_dense", "chi2_aug_state",
 ]
 
 FFT_WORKERS = 1
@@ -390,6 +390,31 @@ class Chain:
                 w = np.where(np.isinf(part.Nbar) | (part.Nbar <= 0), 0.0, 1.0 / part.Nbar)
             tot += _quad(part.name, self.dd[i] - self.t[i], w)
         return tot
+
+
+def chi2_aug_state(chain: "Chain", lam: float) -> float:
+    """The augmented objective (Appendix A, eq. 2mess_prob) of the fields a
+    GPU plan keeps, with the two it does not keep at their conditional means:
+    s given d_0 (merged 2DF block: s = C/(C + N_0) d_0, which the merged
+    sweep already holds) and, when a stripe part sits between them, the pixel
+    messenger given its neighbours d_RF and d,
+        t_PX = (T_PX d + Nbar_PX d_RF) / (Nbar_PX + T_PX)   (d_RF on masked pixels).
+    Minimising over one field cannot raise the objective, so this is at most
+    chain.chi2_aug(lam), with equality at the fixed point."""
+    P = chain.P
+    c = Chain(P)
+    c.s = chain.s.copy()
+    c.t = [t.copy() for t in chain.t]
+    c.dd = [d.copy() for d in chain.dd]
+    if P.merge_2df:
+        N0 = P.parts[0].N
+        c.s = from_basis("2DF", P.C / (P.C + N0) * to_basis("2DF", c.dd[0]))
+        c.t[0] = c.s
+    names = [part.name for part in P.parts]
+    if "RF" in names and names[-1] == "PX":
+        i = len(names) - 1
+        c.t[i] = _link_mean(P.parts[i].Nbar, c.dd[i], c.T(i, lam), c.dd[i - 1])
+    return c.chi2_aug(lam)
 
 
 def _quad(basis: str, x: np.ndarray, w: np.ndarray) -> float:

@@ -186,6 +186,40 @@ def test_augmented_chi2_equals_chi2_at_the_fixed_point():
     assert abs(r["chain"].chi2_aug(1.0) - c) / c < 1e-9
 
 
+def test_state_chi2_aug_minimises_the_unkept_fields():
+    # chi2_aug_state puts s and (with a stripe part) the pixel messenger at
+    # their conditional means: never above chi2_aug of the same state, equal
+    # to it after a merged sweep without a stripe part (nothing to minimise:
+    # the merged sweep already holds s at its mean), equal to chi^2(s*) at
+    # the fixed point, and below it when the pixel messenger is perturbed
+    for kw in (dict(), dict(stripes=False), dict(one_over_f=False), dict(one_over_f=False, stripes=False)):
+        p = _prob(**kw)
+        for merge in (True, False):
+            P = O.build_parts(p, merge_2df=merge)
+            ch = O.Chain(P)
+            for _ in range(3):
+                ch.sweep(10.0)
+            a, b = O.chi2_aug_state(ch, 10.0), ch.chi2_aug(10.0)
+            assert a <= b * (1 + 1e-12), (kw, merge, a, b)
+            names = [q.name for q in P.parts]
+            if P.merge_2df and "RF" not in names:
+                assert abs(a - b) <= 1e-12 * b, (kw, a, b)
+    p = _prob()
+    P = O.build_parts(p, merge_2df=True)
+    ch = O.Chain(P)
+    for _ in range(3):
+        ch.sweep(10.0)
+    base = O.chi2_aug_state(ch, 10.0)
+    ch.t[-1] = ch.t[-1] + 0.3 * np.random.default_rng(5).standard_normal(ch.t[-1].shape)
+    assert O.chi2_aug_state(ch, 10.0) == pytest.approx(base, rel=1e-12)   # t_PX is minimised out
+    assert ch.chi2_aug(10.0) > base
+    p = _rect(seed=13)
+    s_d, M = O.dense_wf(p, return_parts=True)
+    r = _converged(p, tol=1e-11)
+    c = O.chi2(p, s_d, Ninv=M["Ninv"])
+    assert abs(O.chi2_aug_state(r["chain"], 1.0) - c) / c < 1e-9
+
+
 def test_interior_link_with_theta_one_freezes_a_mode():
     # Reading: tau = the exact minimum eigenvalue of an interior part makes
     # Nbar = 0 on that mode; d_i = t_i is then pinned and never moves.
