@@ -294,6 +294,20 @@ WF_API int wf_iterate(wf_plan_t plan, double lam, int n);
 WF_API int wf_residual(wf_plan_t plan, double* rel_rho_u, double* rel_rho_m);
 
 /*
+ * wf_chi2_aug -- the augmented objective of the current iterate (Appendix A,
+ * eq. 2mess_prob: the sum over the chain's links of squared differences over
+ * their covariances), which every update of the iteration lowers at fixed
+ * lambda and which equals chi^2(s) at the fixed point.  The fields the plan
+ * does not keep are at their conditional means: s = C/(C + N_0) d_0 and,
+ * with a stripe part, the pixel messenger given d_RF and d.  Evaluated at the
+ * current lambda, in FP64 from the FP32 fields; *value receives it.
+ * WF_EINVAL without a loaded problem (also after wf_solve with refine > 0,
+ * whose fields belong to the last correction); WF_EUNSUPPORTED for the plain
+ * sweep (merge_2df = 0 with a 1/f part).
+ */
+WF_API int wf_chi2_aug(wf_plan_t plan, double* value);
+
+/*
  * wf_get_field -- write one field of the current state, in pixel space, to
  * out [ny][nx] (device or host).  Fields absent from the plan's parts give
  * WF_EINVAL (and WF_FIELD_T_2DF with merge_2df, where t_2DF is marginalised).

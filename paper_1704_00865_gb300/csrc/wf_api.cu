@@ -42,6 +42,7 @@ struct wf_plan_s {
   float2 *twx = nullptr, *twy = nullptr, *twh = nullptr;  // twh: exp(-2 pi i k/(nx/2))
   float2 *r_g = nullptr, *r_q = nullptr;
   double* part = nullptr;
+  double* chi = nullptr;  // wf_chi2_aug: partial sums, then the value
   WfState* st = nullptr;
   double* lam_sched = nullptr;
   int* it_sched = nullptr;
@@ -258,6 +259,7 @@ int wf_plan_create(wf_plan_t* out, int ny, int nx, unsigned parts, const wf_para
   AL(P->r_g, nh);
   AL(P->r_q, nh);
   AL(P->part, (size_t)3 * P->nrow + 4 * 256 + 64);
+  AL(P->chi, (size_t)chi2_scratch(ny, nx) + 1);
   AL(P->st, (size_t)1);
   AL(P->st_save, (size_t)1);
   AL(P->lam_sched, (size_t)260);
@@ -785,6 +787,34 @@ int wf_run(wf_plan_t P, const wf_schedule* sch, double tol, wf_stats* st) {
   CK(cudaEventRecord(P->ev_out, P->gstream));
   CK(cudaStreamWaitEvent(user, P->ev_out, 0));
   return rc;
+}
+
+int wf_chi2_aug(wf_plan_t P, double* value) {
+  if (!P || !P->loaded || !value) return WF_EINVAL;
+  if (P->has_f && !P->merge) return WF_EUNSUPPORTED;  // the plain sweep's t_2DF links are not summed
+  Chi2Fields f{};
+  f.ny = P->ny;
+  f.nx = P->nx;
+  f.has_rf = P->has_rf;
+  f.d0 = P->f_x;
+  f.t = P->has_rf ? P->f_t1 : P->f_y;
+  f.d1 = P->has_rf ? P->f_d1 : nullptr;
+  f.dn = P->dn;
+  f.eig = P->eig;
+  f.eig_nyq = P->eig_nyq;
+  f.pst = P->pst;
+  f.a2 = P->a2;
+  f.twx = P->twx;
+  f.twy = P->twy;
+  f.st = P->st;
+  const int n = chi2_scratch(P->ny, P->nx);
+  CKI(launch_chi2(f, P->chi, P->chi + n, P->stream));
+  P->launches += 3;
+  double v = 0.0;
+  CK(cudaMemcpyAsync(&v, P->chi + n, sizeof(double), cudaMemcpyDeviceToHost, P->stream));
+  CK(cudaStreamSynchronize(P->stream));
+  *value = v;
+  return WF_OK;
 }
 
 int wf_residual(wf_plan_t P, double* rel_u, double* rel_m) {

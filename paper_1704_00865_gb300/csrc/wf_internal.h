@@ -203,6 +203,24 @@ int launch_pack_data(float4* dn_out, const float4* dn_in, const float2* rho, siz
 int launch_sub(float* y, const float* x, size_t n, cudaStream_t s);
 // y[i] = v;  y[i] = a x[i]
 int launch_fill(float* y, float v, size_t n, cudaStream_t s);
+
+// augmented objective of the kept fields (wf_chi.cu)
+struct Chi2Fields {
+  int ny, nx, has_rf;
+  const float2* d0;           // d_2DF (or s) in RF, column-tiled
+  const float2* t;            // t_RF (stripe part) or t_PX, RF, column-tiled
+  const float2* d1;           // d_RF row-major, or nullptr
+  const float4* dn;
+  const float2* eig;
+  const float2* eig_nyq;
+  const float* pst;
+  const float* a2;
+  const float2* twx;
+  const float2* twy;
+  const WfState* st;
+};
+int chi2_scratch(int ny, int nx);  // doubles of scratch launch_chi2 needs (0: unsupported size)
+int launch_chi2(const Chi2Fields& f, double* scratch, double* out, cudaStream_t s);
 int launch_scale(float* y, const float* x, float a, size_t n, cudaStream_t s);
 
 }  // namespace wf

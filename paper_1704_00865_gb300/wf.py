@@ -25,7 +25,7 @@ WF_FIELD_S, WF_FIELD_T_2DF, WF_FIELD_D_2DF, WF_FIELD_T_RF, WF_FIELD_D_RF = range
 
 # every symbol include/wf.h declares
 EXPORTS = ["wf_version", "wf_strerror", "wf_params_default", "wf_plan_create", "wf_plan_destroy",
-           "wf_set_problem", "wf_run", "wf_iterate", "wf_residual", "wf_get_field", "wf_solve",
+           "wf_set_problem", "wf_run", "wf_iterate", "wf_residual", "wf_chi2_aug", "wf_get_field", "wf_solve",
            "wf_fft2", "wf_launch_count", "wf_time_passes", "wf_fft2_noalloc",
            "wf_batch_create", "wf_batch_destroy", "wf_batch_solve", "wf_batch_launch_count",
            "wf_fno_create", "wf_fno_destroy", "wf_fno_num_params", "wf_fno_forward", "wf_fno_gradient",
@@ -99,6 +99,7 @@ def load(path: Optional[str] = None):
     L.wf_run.argtypes = [vp, C.POINTER(wf_schedule), C.c_double, C.POINTER(wf_stats)]
     L.wf_iterate.argtypes = [vp, C.c_double, C.c_int]
     L.wf_residual.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+    L.wf_chi2_aug.argtypes = [vp, C.POINTER(C.c_double)]
     L.wf_get_field.argtypes = [vp, C.c_int, vp]
     L.wf_solve.argtypes = [vp] + [vp] * 7 + [C.POINTER(wf_schedule), C.c_double, vp, C.POINTER(wf_stats)]
     L.wf_fft2.argtypes = [vp, vp, vp, C.c_int, C.c_int]
@@ -316,6 +317,12 @@ class Plan:
         u, m = C.c_double(), C.c_double()
         _check(load().wf_residual(self.h, C.byref(u), C.byref(m)), "wf_residual")
         return u.value, m.value
+
+    def chi2_aug(self) -> float:
+        """Augmented objective of the current iterate (wf_chi2_aug)."""
+        v = C.c_double()
+        _check(load().wf_chi2_aug(self.h, C.byref(v)), "wf_chi2_aug")
+        return v.value
 
     def get_field(self, field: int, out=None):
         if out is None:

@@ -340,3 +340,35 @@ def test_extra_corrections_run_only_while_the_stop_test_fails(wf):
     a, sa = _solve_refined(wf, prob, sched2, 1e-5, 1, **big)
     b, sb = _solve_refined(wf, prob, sched2, 1e-5, 1, refine_extra=8, **big)
     assert sa["status"] == 0 and sb["iters"] == sa["iters"] and np.array_equal(a, b), (sa, sb)
+
+
+@pytest.mark.parametrize("name", list(CONFIGS))
+@pytest.mark.parametrize("shape", [(64, 128), (128, 32)])
+def test_chi2_aug_matches_the_oracle(wf, name, shape):
+    # Appendix A: the augmented objective of the kept fields (s and, with a
+    # stripe part, the pixel messenger at their conditional means) after each
+    # sweep, against the oracle's for the same state; at fixed lambda no
+    # sweep raises it
+    prob = synth.make_problem(*shape, 12, mask_frac=0.05, **CONFIGS[name])
+    plan = make_plan(prob, merge_2df=1, split_f=0.5, split_fp=0.5)
+    P = O.build_parts(prob, merge_2df=True, split_f=0.5, split_fp=0.5)
+    ch = O.Chain(P)
+    vals = []
+    for lam in (30.0, 30.0, 30.0, 3.0):
+        plan.iterate(lam, 1)
+        ch.sweep(lam)
+        g, r = plan.chi2_aug(), O.chi2_aug_state(ch, lam)
+        assert abs(g - r) < 1e-4 * r, (name, lam, g, r)
+        vals.append(g)
+    assert vals[1] <= vals[0] and vals[2] <= vals[1], vals
+    plan.close()
+
+
+def test_chi2_aug_needs_the_merged_block(wf):
+    prob = synth.make_problem(64, 64, 13, mask_frac=0.05)
+    plan = make_plan(prob, merge_2df=0, split_f=0.5, split_fp=0.3)
+    plan.iterate(10.0, 2)
+    with pytest.raises(wf.WFError) as e:
+        plan.chi2_aug()
+    assert e.value.code == wf.WF_EUNSUPPORTED
+    plan.close()
