@@ -405,7 +405,9 @@ def run_gpu(args):
 
 
 # ------------------------------------------------------------- batched form
-BATCH_SIZES = [256, 512, 1024, 2048]   # power-of-two part of the uneven-size mix
+# the uneven-size mix (lengths 2^k and 3 * 2^k); 32 seeded maps bound one
+# batch to a few seconds (a 512-map batch takes about 100 s per step)
+BATCH_SIZES = [256, 384, 512, 768, 1024, 1536, 2048]
 BATCH_MAPS = 32
 BATCH_LANES = 8
 
