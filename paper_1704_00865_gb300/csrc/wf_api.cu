@@ -1005,7 +1005,7 @@ static int solve_impl(wf_plan_t P, const float* d, const float* pixel_var, const
     return WF_OK;
   };
   // residual of the refined s against the original problem, into h_st
-  auto judge = [&]() -> int {
+  auto residual_of_refined = [&]() -> int {
     int rc2 = enqueue_resid_map(P, P->s_acc, P->rho, nullptr);
     if (rc2) return rc2;
     CK(cudaMemcpyAsync(&P->st->du2, &du2, sizeof(double), cudaMemcpyHostToDevice, P->stream));
@@ -1020,11 +1020,11 @@ static int solve_impl(wf_plan_t P, const float* d, const float* pixel_var, const
   auto passes = [&]() { return P->h_st->rel_u <= tol * P->p.tol_u_scale && P->h_st->rel_m <= tol; };
   for (int r = 0; r < P->p.refine; ++r)
     if ((rc = correct())) return rc;
-  if ((rc = judge())) return rc;
+  if ((rc = residual_of_refined())) return rc;
   // further corrections only while the refined s fails the stop test
   for (int r = 0; tol > 0 && r < P->p.refine_extra && !passes(); ++r) {
     if ((rc = correct())) return rc;
-    if ((rc = judge())) return rc;
+    if ((rc = residual_of_refined())) return rc;
   }
   const bool dev = is_device_ptr(s_out);
   CK(cudaMemcpyAsync(s_out, P->s_acc, npx * sizeof(float), dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
