@@ -180,9 +180,9 @@ row_kernel(RowArgs a) {
 
 
 // Row pass geometry: each row is one real length-2M transform done by TPF
-// threads with E values each -- a single warp per row up to M = 512, so the
-// exchange steps need only warp barriers.  Short rows are packed several to
-// a warp.  One CTA = ROWS rows; the grid is ny / ROWS CTAs, small enough
+// threads with E values each -- a single warp per row up to M = 256 with 8
+// values per thread (then the exchange steps need only warp barriers), two
+// warps at M = 512.  Short rows are packed several to a warp.  One CTA = ROWS rows; the grid is ny / ROWS CTAs, small enough
 // units that the SMs finish within one row of each other.
 // Values per thread of the two shapes the autotuner chooses between (one
 // where both coincide): 8 (two warps per 1024-point row) measured fastest at
