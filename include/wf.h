@@ -27,14 +27,17 @@
  * and kx = nx/2 must be symmetric in ky (a real covariance); others need not.
  *
  * Memory: every array argument may be a device pointer or a host pointer;
- * the library asks the CUDA runtime which one it is.  Host arrays are copied
+ * the library asks the CUDA runtime which one it is; device memory must
+ * belong to the current device (another GPU's memory gives WF_EINVAL, since
+ * without peer access a kernel touching it faults).  Host arrays are copied
  * to the plan's device workspace (and s_out back) on the plan's stream.
  * The caller keeps ownership of every array.  All calls are stream-ordered
  * on the plan's stream; calls that return results (wf_solve, wf_run,
  * wf_residual, wf_get_field, wf_fft2) synchronise that stream before they
  * return.  A plan is not thread-safe: use one plan per host thread.
  *
- * Sizes: nx and ny are powers of two in [32, 4096].
+ * Sizes: nx and ny are each a power of two in [32, 4096] or one of 384, 768,
+ * 1536 (3 x 2^k: the transforms then take one radix-3 stage).
  *
  * Errors: every function returns WF_OK (0) or one of the codes below;
  * wf_strerror() gives a message.  On error nothing is written to outputs
@@ -377,7 +380,8 @@ WF_API int wf_time_passes(wf_plan_t plan, double lam, int n, double* us_row,
  * cudaMalloc -- a library embedded in a host application whose allocator owns
  * all device memory, or a pipeline that must not allocate once it is running
  * (an allocation can block, fail or synchronise the device at a bad moment).
- *   ny, nx   powers of two in [32, 4096] with ny * nx <= 1048576
+ *   ny, nx   sizes as for wf_plan_create (powers of two in [32, 4096], or
+ *            384, 768, 1536) with ny * nx <= 1048576
  *            (WF_EUNSUPPORTED otherwise)
  *   in, out  device arrays owned by the caller, laid out as for wf_fft2
  *            (host pointers give WF_EINVAL)

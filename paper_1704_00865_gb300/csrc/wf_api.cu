@@ -22,6 +22,7 @@
 #include "../../include/wf.h"
 #include "wf_device.cuh"
 #include "wf_internal.h"
+#include "wf_ptr.h"
 
 using namespace wf;
 
@@ -109,15 +110,15 @@ static int dalloc(wf_plan_s* P, T** out, size_t n) {
   return WF_OK;
 }
 
-static bool is_device_ptr(const void* p) {
-  if (!p) return false;
-  cudaPointerAttributes at;
-  cudaError_t e = cudaPointerGetAttributes(&at, p);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+// where a caller's array lives (wf_ptr.h); another GPU's memory is rejected
+static int ptr_where(const void* p) {
+  if (!p) return PTR_HOST;
+  cudaPointerAttributes at{};
+  const cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) cudaGetLastError();
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) cudaGetLastError();
+  return classify_ptr(e == cudaSuccess, (int)at.type, at.device, cur);
 }
 
 // device view of a caller array: the array itself, or a staged copy
@@ -127,7 +128,9 @@ static int to_device(wf_plan_s* P, const T* src, T* stage, size_t n, const T** o
     *out = nullptr;
     return WF_OK;
   }
-  if (is_device_ptr(src)) {
+  const int where = ptr_where(src);
+  if (where == PTR_OTHER_DEVICE) return WF_EINVAL;
+  if (where == PTR_DEVICE) {
     *out = src;
     return WF_OK;
   }
@@ -836,7 +839,9 @@ int wf_residual(wf_plan_t P, double* rel_u, double* rel_m) {
 
 int wf_get_field(wf_plan_t P, int field, float* out) {
   if (!P || !P->loaded || !out) return WF_EINVAL;
-  const bool dev = is_device_ptr(out);
+  const int where_ = ptr_where(out);
+  if (where_ == PTR_OTHER_DEVICE) return WF_EINVAL;
+  const bool dev = where_ == PTR_DEVICE;
   float2* dst = dev ? (float2*)out : (float2*)P->stg_io;
   RowArgs ra = row_args(P);
   ra.out_px = dst;
@@ -915,6 +920,7 @@ static int solve_impl(wf_plan_t P, const float* d, const float* pixel_var, const
                       const float* P1f, const float* Pst, const float* stripe_amp2, const float* s_init,
                       const wf_schedule* sched, double tol, float* s_out, wf_stats* st) {
   if (!P || !s_out || !sched) return WF_EINVAL;
+  if (ptr_where(s_out) == PTR_OTHER_DEVICE) return WF_EINVAL;
   int rc = wf_set_problem(P, d, pixel_var, mask, C, P1f, Pst, stripe_amp2);
   if (rc) return rc;
   if (s_init && (rc = warm_init(P, s_init))) return rc;
@@ -1026,7 +1032,9 @@ static int solve_impl(wf_plan_t P, const float* d, const float* pixel_var, const
     if ((rc = correct())) return rc;
     if ((rc = residual_of_refined())) return rc;
   }
-  const bool dev = is_device_ptr(s_out);
+  const int where_ = ptr_where(s_out);
+  if (where_ == PTR_OTHER_DEVICE) return WF_EINVAL;
+  const bool dev = where_ == PTR_DEVICE;
   CK(cudaMemcpyAsync(s_out, P->s_acc, npx * sizeof(float), dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                      P->stream));
   CK(cudaStreamSynchronize(P->stream));
@@ -1063,7 +1071,9 @@ int wf_inverse_noise(wf_plan_t P, const float* d, const float* pixel_var, const 
   int rc = solve_impl(P, d, pixel_var, mask, P->stg_C, P1f, Pst, stripe_amp2, nullptr, sched, tol, P->stg_io, st);
   if (rc != WF_OK && rc != WF_ENOCONV && rc != WF_ESTALL) return rc;
   // N^-1 d ~ alpha^-1 [alpha (alpha I + N)^-1 d]
-  const bool dev = is_device_ptr(out);
+  const int where_ = ptr_where(out);
+  if (where_ == PTR_OTHER_DEVICE) return WF_EINVAL;
+  const bool dev = where_ == PTR_DEVICE;
   float* dst = dev ? out : P->stg_io;
   CKI(launch_scale(dst, P->stg_io, (float)(1.0 / alpha), npx, P->stream));
   P->launches += 1;
@@ -1085,7 +1095,9 @@ int wf_fft2(wf_plan_t P, const float* in, float* out, int inverse, int rows_only
   const float* din;
   int rc = to_device(P, in, P->stg_d, n, &din);
   if (rc) return rc;
-  const bool dev = is_device_ptr(out);
+  const int where_ = ptr_where(out);
+  if (where_ == PTR_OTHER_DEVICE) return WF_EINVAL;
+  const bool dev = where_ == PTR_DEVICE;
   float* dout = dev ? out : P->stg_io;
   RowArgs ra = row_args(P);
   ColArgs ca = col_args(P, 0);

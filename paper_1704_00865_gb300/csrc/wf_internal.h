@@ -46,8 +46,9 @@ inline int launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t sm
   at[0].val.programmaticStreamSerializationAllowed = WF_PDL;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, args...);
-  return (int)(e != cudaSuccess ? e : cudaGetLastError());
+  // the return value is this launch's own status (an error left pending by
+  // an earlier, unrelated call is not collected here)
+  return (int)cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 __host__ __device__ __forceinline__ size_t tidx(int y, int kx, int ny) {
   return (size_t)(kx / WF_TW) * ny * WF_TW + (size_t)y * WF_TW + (kx % WF_TW);

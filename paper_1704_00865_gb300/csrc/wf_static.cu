@@ -20,6 +20,7 @@
 
 #include "../../include/wf.h"
 #include "wf_internal.h"
+#include "wf_ptr.h"
 
 namespace {
 
@@ -70,13 +71,15 @@ int static_base(float2** out) {
   return WF_OK;
 }
 
+// device memory of the current GPU (or managed memory); host memory and
+// another GPU's memory are rejected
 bool on_device(const void* p) {
-  cudaPointerAttributes at;
-  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  cudaPointerAttributes at{};
+  const cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) cudaGetLastError();
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) cudaGetLastError();
+  return wf::classify_ptr(e == cudaSuccess, (int)at.type, at.device, cur) == wf::PTR_DEVICE;
 }
 
 }  // namespace
@@ -94,8 +97,13 @@ extern "C" int wf_fft2_noalloc(int ny, int nx, const float* in, float* out, int 
   float2* twy = base + kMaxSide;
   float2* spec = base + 2 * kMaxSide;
   const int nmax = nx > ny ? nx : ny;
-  static_twiddles<<<(nmax + 255) / 256, 256, 0, s>>>(base, nx, ny);
-  if (cudaGetLastError() != cudaSuccess) return WF_ECUDA;
+  // launched with cudaLaunchKernelEx, whose return value is this launch's
+  // own status (an error some earlier call left pending is not collected)
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((nmax + 255) / 256);
+  cfg.blockDim = dim3(256);
+  cfg.stream = s;
+  if (cudaLaunchKernelEx(&cfg, static_twiddles, base, nx, ny) != cudaSuccess) return WF_ECUDA;
 
   wf::RowArgs ra{};
   ra.ny = ny;

@@ -400,7 +400,13 @@ class Plan:
 
 def wf_fft2_noalloc(ny: int, nx: int, x, out, inverse: bool = False, stream=None):
     """The 2D transform without a plan or any device allocation (device
-    tensors in and out; see include/wf.h).  Returns after launching."""
+    tensors in and out; see include/wf.h).  Returns after launching.  x must
+    already be a contiguous float32 tensor: a converted copy would be a
+    temporary allocation that could be freed while the transform, queued on
+    `stream`, still reads it."""
+    import torch
+    if not (isinstance(x, torch.Tensor) and x.dtype == torch.float32 and x.is_contiguous()):
+        raise ValueError("wf_fft2_noalloc: x must be a contiguous float32 tensor")
     pi, ki = _ptr(x, np.float32, ny * nx)
     po, ko = _ptr(out, np.float32, ny * nx, writable=True)
     _check(load().wf_fft2_noalloc(int(ny), int(nx), pi, po, int(bool(inverse)),

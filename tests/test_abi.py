@@ -139,3 +139,45 @@ def test_batch_solve_rejects_null_handles(lib):
     assert lib.wf_batch_launch_count(None) == -1
     lib.wf_batch_destroy(None)
     assert C.sizeof(wf.wf_map) == 8 * 8
+
+
+def test_pointer_rule_rejects_another_gpus_memory(tmp_path):
+    # The rule every entry point applies to a caller's array (csrc/wf_ptr.h),
+    # from what cudaPointerGetAttributes reports: device memory of the current
+    # GPU is used in place, host memory is staged, and device memory of any
+    # other GPU is rejected (WF_EINVAL) instead of being handed to a kernel
+    # that would fault on it.  Compiled here with the host compiler alone.
+    import shutil
+    import subprocess
+    cxx = shutil.which("g++") or shutil.which("c++")
+    if cxx is None:
+        pytest.skip("no host C++ compiler")
+    src = tmp_path / "ptr_rule.cpp"
+    src.write_text(r'''
+#include <cstdio>
+#include "wf_ptr.h"
+using namespace wf;
+int main() {
+  int bad = 0;
+  // (query ok, cudaMemoryType, pointer's device, current device) -> where
+  struct { bool ok; int type, pdev, cur, want; } cases[] = {
+    {true, 2, 0, 0, PTR_DEVICE},        // this GPU's memory
+    {true, 2, 3, 3, PTR_DEVICE},
+    {true, 2, 1, 0, PTR_OTHER_DEVICE},  // a second GPU's memory
+    {true, 2, 0, 1, PTR_OTHER_DEVICE},
+    {true, 3, 1, 0, PTR_DEVICE},        // managed memory, any device
+    {true, 1, 0, 0, PTR_HOST},          // pinned host memory
+    {true, 0, -2, 0, PTR_HOST},         // pageable host memory
+    {false, 0, 0, 0, PTR_HOST},         // query failed: not device memory
+  };
+  for (auto& c : cases)
+    if (classify_ptr(c.ok, c.type, c.pdev, c.cur) != c.want) { std::printf("case %d %d %d\n", c.type, c.pdev, c.cur); ++bad; }
+  return bad;
+}
+''')
+    exe = tmp_path / "ptr_rule"
+    inc = os.path.join(ROOT, "paper_1704_00865_gb300", "csrc")
+    r = subprocess.run([cxx, "-std=c++17", "-I", inc, str(src), "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout

@@ -120,6 +120,19 @@ def test_dense_solution_minimises_chi2():
         assert O.chi2(p, s + delta, Ninv=M["Ninv"]) > c0
 
 
+def test_chi2_by_conjugate_gradients_equals_the_dense_value():
+    # chi2() without a dense N^-1 solves N_uu x = (d - s)_u by CG (the path a
+    # full-size map takes); on a tiny masked map with per-row stripe
+    # amplitudes it must give the value the dense masked N^-1 gives, at the
+    # solution and away from it
+    p = _prob(stripe_rows_vary=True)
+    s_d, M = O.dense_wf(p, return_parts=True)
+    rng = np.random.default_rng(12)
+    for s in (s_d, s_d + 1e-2 * np.std(s_d) * rng.standard_normal(s_d.shape), np.zeros_like(s_d)):
+        ref = O.chi2(p, s, Ninv=M["Ninv"])
+        assert abs(O.chi2(p, s) - ref) / ref < 1e-9, (O.chi2(p, s), ref)
+
+
 @pytest.mark.parametrize("shape", [(8, 12), (12, 8)])
 def test_messenger_converges_to_dense_three_parts_mask_row_amplitudes(shape):
     p = _rect(*shape, stripe_rows_vary=True)

@@ -17,7 +17,7 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-@pytest.mark.parametrize("ny,nx", [(1024, 1024), (64, 256)])
+@pytest.mark.parametrize("ny,nx", [(1024, 1024), (64, 256), (384, 1536)])
 def test_noalloc_transform_matches_plan_transform_on_two_calls(ny, nx):
     import torch
     from paper_1704_00865_gb300 import build, wf
@@ -56,3 +56,26 @@ def test_noalloc_rejects_sizes_beyond_its_array_and_host_buffers():
     dev = torch.empty(64 * 64, device="cuda")
     assert lib.wf_fft2_noalloc(64, 64, wf.C.c_void_p(host.ctypes.data), wf.C.c_void_p(dev.data_ptr()),
                                0, None) == wf.WF_EINVAL
+
+
+def test_noalloc_call_after_a_larger_one_rewrites_what_it_reads():
+    # the shared array keeps the last call's contents: a 64 x 256 transform
+    # after a 1024 x 1024 one (and a 1024 x 1024 one after that) must read
+    # only what it wrote itself -- every twiddle and spectrum entry it uses
+    import torch
+    from paper_1704_00865_gb300 import build, wf
+    build.build()
+    wf.load()
+    stream = torch.cuda.current_stream()
+    sp = wf.C.c_void_p(stream.cuda_stream)
+    rng = np.random.default_rng(7)
+    for ny, nx in [(1024, 1024), (64, 256), (1024, 1024)]:
+        plan = wf.Plan(ny, nx, wf.WF_PART_WHITE)
+        for inverse in (False, True):
+            x = rng.standard_normal((ny, nx)).astype(np.float32)
+            ref = plan.fft2(x, inverse=inverse)
+            out = torch.empty(ny * nx, device="cuda")
+            wf.wf_fft2_noalloc(ny, nx, torch.from_numpy(x).cuda(), out, inverse=inverse, stream=sp)
+            stream.synchronize()
+            assert _rel(out.cpu().numpy(), ref) < 5e-6, (ny, nx, inverse)
+        plan.close()
