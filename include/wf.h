@@ -53,7 +53,7 @@
 extern "C" {
 #endif
 
-#define WF_ABI_VERSION 1
+#define WF_ABI_VERSION 2
 
 #if defined(__GNUC__)
 #define WF_API __attribute__((visibility("default")))
@@ -190,6 +190,17 @@ typedef struct {
  *                  ny in {512, 1024, 2048, 4096} and merge_2df = 1
  *                  (WF_EUNSUPPORTED otherwise); the column shape is then the
  *                  16-value one.
+ *  sweep_kernel    how a sweep is launched: 0 (default) as one cooperative
+ *                  launch per residual_every sweeps where the plan allows it
+ *                  (1024 x 1024 maps with a stripe part, the merged 2DF block
+ *                  or no 1/f part, dft_precision 0, a GPU with at least 128
+ *                  SMs), else as a row-pass and a column-pass launch per
+ *                  sweep; 1 always the two launches; 2 always one launch
+ *                  (WF_EUNSUPPORTED from wf_plan_create where it cannot).
+ *                  In the one-launch form every CTA keeps the tables and
+ *                  fields of its own rows and column tile in shared memory
+ *                  across sweeps; the arithmetic is that of the two
+ *                  launches, with 8 values per thread in both transforms.
  */
 typedef struct {
   double theta[3];
@@ -209,6 +220,7 @@ typedef struct {
   int autotune;
   int dft_precision;
   int refine_extra;
+  int sweep_kernel;
 } wf_params;
 
 /* Results of a solve. */
@@ -372,6 +384,17 @@ WF_API int wf_plan_shapes(wf_plan_t plan, int* row_values, int* col_values);
  */
 WF_API int wf_time_passes(wf_plan_t plan, double lam, int n, double* us_row,
                           double* us_col);
+
+/*
+ * wf_time_sweeps -- measurement aid: at fixed lambda, capture n sweeps as the
+ * plan's iteration launches them (one cooperative launch, or n row-pass /
+ * column-pass pairs; see wf_params.sweep_kernel) in a CUDA graph and time its
+ * replay with CUDA events; *us_per_sweep receives the mean time per sweep
+ * in microseconds and *one_launch (if not NULL) 1 for the one-launch form.
+ * The sweeps overwrite the state: load the plan again (wf_set_problem)
+ * before further iteration.
+ */
+WF_API int wf_time_sweeps(wf_plan_t plan, double lam, int n, double* us_per_sweep, int* one_launch);
 
 /*
  * wf_fft2_noalloc -- the forward or inverse 2D transform of wf_fft2 without a

@@ -30,6 +30,7 @@ struct wf_plan_s {
   int ny = 0, nx = 0, M = 0;
   unsigned parts = 0;
   bool has_f = false, has_rf = false, merge = false, loaded = false;
+  bool fused = false;       // sweeps run as one cooperative launch (wf_fused.cu)
   wf_params p{};
   cudaStream_t stream = nullptr;
   int nrow = 0;
@@ -44,6 +45,7 @@ struct wf_plan_s {
   float2 *r_g = nullptr, *r_q = nullptr;
   double* part = nullptr;
   double* chi = nullptr;  // wf_chi2_aug: partial sums, then the value
+  unsigned* fbar = nullptr;  // grid barrier words of the one-launch sweep
   WfState* st = nullptr;
   double* lam_sched = nullptr;
   int* it_sched = nullptr;
@@ -210,7 +212,7 @@ int wf::check_plan_args(int ny, int nx, unsigned parts, const wf_params* p) {
   if (prm.refine < 0 || prm.refine > 8 || !(prm.refine_tol_scale >= 1.0) || prm.refine_max_iters < 0 ||
       prm.refine_lam1_iters < 0 || prm.stall_checks < 0 || prm.autotune < 0 || prm.autotune > 2 ||
       prm.refine_extra < 0 || prm.refine_extra > 8 ||
-      prm.dft_precision < 0 || prm.dft_precision > 2)
+      prm.dft_precision < 0 || prm.dft_precision > 2 || prm.sweep_kernel < 0 || prm.sweep_kernel > 2)
     return WF_EINVAL;
   // tensor-core radix-16 stages: 16-value column shapes, merged 2DF block
   if (prm.dft_precision != 0 && (!col_tc_supported(ny) || prm.merge_2df != 1)) return WF_EUNSUPPORTED;
@@ -264,6 +266,7 @@ int wf_plan_create(wf_plan_t* out, int ny, int nx, unsigned parts, const wf_para
   AL(P->part, (size_t)3 * P->nrow + 4 * 256 + 64);
   AL(P->chi, (size_t)chi2_scratch(ny, nx) + 1);
   AL(P->st, (size_t)1);
+  AL(P->fbar, (size_t)4);
   AL(P->st_save, (size_t)1);
   AL(P->lam_sched, (size_t)260);
   AL(P->it_sched, (size_t)260);
@@ -300,6 +303,19 @@ int wf_plan_create(wf_plan_t* out, int ny, int nx, unsigned parts, const wf_para
     cudaGetLastError();
     wf_plan_destroy(P);
     return WF_ECUDA;
+  }
+  if (cudaMemset(P->fbar, 0, 4 * sizeof(unsigned)) != cudaSuccess) {
+    cudaGetLastError();
+    wf_plan_destroy(P);
+    return WF_ECUDA;
+  }
+  // one launch per R sweeps where the map fits it (or when asked to)
+  if (prm.sweep_kernel != 1) {
+    P->fused = fused_supported(ny, nx, P->has_rf, P->merge || !P->has_f, prm.dft_precision);
+    if (!P->fused && prm.sweep_kernel == 2) {
+      wf_plan_destroy(P);
+      return WF_EUNSUPPORTED;
+    }
   }
   // twiddle tables exp(-2 pi i k / n), computed in double on the host
   std::vector<float2> tx(nx), ty(ny);
@@ -395,6 +411,39 @@ static int enqueue_iteration(wf_plan_s* P, int parity) {
   int rc = enqueue_row_pass(P);
   if (rc) return rc;
   return enqueue_col_pass(P, parity);
+}
+
+// n sweeps from a sweep of the given parity: one cooperative launch for a
+// fused plan, else n row-pass / column-pass pairs
+static int enqueue_sweeps(wf_plan_s* P, int n, long long first) {
+  if (!P->fused) {
+    for (int i = 0; i < n; ++i) {
+      int rc = enqueue_iteration(P, (int)((first + i) & 1));
+      if (rc) return rc;
+    }
+    return WF_OK;
+  }
+  FusedArgs f{};
+  f.ny = P->ny;
+  f.nx = P->nx;
+  f.nsweeps = n;
+  f.dn = P->dn;
+  f.f_d1 = P->f_d1;
+  f.f_t1 = P->f_t1;
+  f.f_x = P->f_x;
+  f.eig = P->eig;
+  f.eig_nyq = P->eig_nyq;
+  f.pst = P->pst;
+  f.a2 = P->a2;
+  f.twx = P->twx;
+  f.twh = P->twh;
+  f.twy = P->twy;
+  f.src = P->has_src ? P->src_2df : nullptr;
+  f.st = P->st;
+  f.bar = P->fbar;
+  CKI(launch_fused(f, P->stream));
+  P->launches += 1;
+  return WF_OK;
 }
 
 // residual passes; partials land in part[0 .. 3 nrow)
@@ -601,6 +650,7 @@ int wf_set_problem(wf_plan_t P, const float* d, const float* pixel_var, const ui
   a.has_f = P->has_f;
   a.merge = P->merge;
   CK(cudaMemsetAsync(P->st, 0, sizeof(WfState), P->stream));
+  CK(cudaMemsetAsync(P->fbar, 0, 4 * sizeof(unsigned), P->stream));
   CKI(launch_setup(a, P->stream));
   P->launches += 5;
   // iteration starts from zero fields (Sec. 2)
@@ -626,12 +676,9 @@ int wf_iterate(wf_plan_t P, double lam, int n) {
   if (!P || !P->loaded || n < 0 || !(lam >= 1.0) || !isfinite(lam)) return WF_EINVAL;
   CKI(launch_set_lambda(P->st, lam, 1, P->stream));
   P->launches += 1;
-  for (int i = 0; i < n; ++i) {
-    int rc = enqueue_iteration(P, (int)(P->it_done & 1));
-    if (rc) return rc;
-    P->it_done++;
-  }
-  CK(cudaGetLastError());
+  int rc = enqueue_sweeps(P, n, P->it_done);
+  if (rc) return rc;
+  P->it_done += n;
   return WF_OK;
 }
 
@@ -695,12 +742,10 @@ static int wf_run_on(wf_plan_t P, const wf_schedule* sch, double tol, wf_stats* 
   auto enqueue_chunk = [&](long long start) -> int {
     long long e = start;
     for (int cp = 0; cp < K && e < cap; ++cp) {
-      for (int i = 0; i < R; ++i) {
-        int rc = enqueue_iteration(P, (int)(e & 1));
-        if (rc) return rc;
-        ++e;
-      }
-      int rc = enqueue_residual(P, (int)(e & 1), 1);
+      int rc = enqueue_sweeps(P, R, e);
+      if (rc) return rc;
+      e += R;
+      rc = enqueue_residual(P, (int)(e & 1), 1);
       if (rc) return rc;
       CKI(launch_ctrl(c, P->stream));
       P->launches += 1;
@@ -1189,6 +1234,50 @@ int wf_time_passes(wf_plan_t P, double lam, int n, double* us_row, double* us_co
   if (rc) return rc;
   if (us_row) *us_row = res[0];
   if (us_col) *us_col = res[1];
+  return WF_OK;
+}
+
+int wf_time_sweeps(wf_plan_t P, double lam, int n, double* us_per_sweep, int* one_launch) {
+  if (!P || !P->loaded || n < 1 || !(lam >= 1.0) || !isfinite(lam)) return WF_EINVAL;
+  // n sweeps as the plan's iteration runs them (one cooperative launch, or
+  // n row-pass / column-pass pairs), captured in a graph on the plan's
+  // stream and timed by events around its replay
+  cudaStream_t user = P->stream;
+  P->stream = P->gstream;
+  int rc = WF_OK;
+  float ms = 0.f;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = WF_ECUDA;
+  if (!rc && launch_set_lambda(P->st, lam, 1, P->stream)) rc = WF_ECUDA;
+  if (!rc) rc = enqueue_sweeps(P, 1, P->it_done);  // un-captured first: kernel attributes
+  if (!rc && cudaStreamBeginCapture(P->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = WF_ECUDA;
+  if (!rc) {
+    rc = enqueue_sweeps(P, n, P->it_done);
+    cudaError_t ce = cudaStreamEndCapture(P->stream, &g);
+    if (!rc && (ce != cudaSuccess || cudaGraphInstantiate(&ge, g, 0) != cudaSuccess)) rc = WF_ECUDA;
+  }
+  if (!rc && (cudaGraphLaunch(ge, P->stream) != cudaSuccess ||  // warm
+              cudaEventRecord(e0, P->stream) != cudaSuccess || cudaGraphLaunch(ge, P->stream) != cudaSuccess ||
+              cudaEventRecord(e1, P->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+              cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+    rc = WF_ECUDA;
+  if (ge) cudaGraphExecDestroy(ge);
+  if (g) cudaGraphDestroy(g);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (rc) cudaGetLastError();
+  cudaStreamSynchronize(P->stream);
+  P->stream = user;
+  // the state has moved on by 2n + 1 sweeps
+  P->loaded = false;
+  if (!rc && P->h_st && cudaMemcpy(P->h_st, P->st, sizeof(WfState), cudaMemcpyDeviceToHost) == cudaSuccess &&
+      (P->h_st->err & WF_ERR_TIMEOUT))
+    rc = WF_ETIMEOUT;
+  if (rc) return rc;
+  if (us_per_sweep) *us_per_sweep = 1000.0 * ms / n;
+  if (one_launch) *one_launch = P->fused ? 1 : 0;
   return WF_OK;
 }
 

@@ -200,39 +200,11 @@ col_pass_kernel(ColArgs a) {
   for (int m = 0; m < E; ++m) {
     const int k = t + m * TPC;
     const float2 eg = s_eig[Cfg::sidx(k, c)];
-    if constexpr (MODE == COL_PASS_MERGE) {
-      // joint update of the 2DF block given y (Appendix A shortcut):
-      // d_2DF = (C + N0)/(C + N0 + T) y, s = C/(C + N0) d_2DF implicit
-      const float pa = eg.x + eg.y + off0;
-      if (packed) {
-        const float2 egb = egn[m];
-        const float pb = egb.x + egb.y + off0;
-        float2 A, B;
-        unpack_pair(v[m], vp[m], A, B);
-        v[m] = repack_pair(cscale(A, __fdividef(pa, pa + Tl)), cscale(B, __fdividef(pb, pb + Tl)));
-      } else {
-        v[m] = cscale(v[m], __fdividef(pa, pa + Tl));
-      }
-    } else if constexpr (MODE == COL_PASS_MERGE_SRC) {
-      // the same block with a source j in the objective (-2 s.j): the joint
-      // minimiser is d_2DF = ((C + N0) y + T C j^) / (C + N0 + T)
-      const float pa = eg.x + eg.y + off0;
-      const float2 jv = s_t0[Cfg::sidx(k, c)];
-      if (packed) {
-        const float2 egb = egn[m];
-        const float pb = egb.x + egb.y + off0;
-        const float2 jp = s_t0[Cfg::sidx(neg_mod<L>(k), c)];
-        float2 A, B, JA, JB;
-        unpack_pair(v[m], vp[m], A, B);
-        unpack_pair(jv, jp, JA, JB);
-        const float ia = __fdividef(1.f, pa + Tl), ib = __fdividef(1.f, pb + Tl);
-        const float2 dA = make_float2((pa * A.x + Tl * eg.x * JA.x) * ia, (pa * A.y + Tl * eg.x * JA.y) * ia);
-        const float2 dB = make_float2((pb * B.x + Tl * egb.x * JB.x) * ib, (pb * B.y + Tl * egb.x * JB.y) * ib);
-        v[m] = repack_pair(dA, dB);
-      } else {
-        const float ia = __fdividef(1.f, pa + Tl);
-        v[m] = make_float2((pa * v[m].x + Tl * eg.x * jv.x) * ia, (pa * v[m].y + Tl * eg.x * jv.y) * ia);
-      }
+    if constexpr (MODE == COL_PASS_MERGE || MODE == COL_PASS_MERGE_SRC) {
+      constexpr bool SRC = (MODE == COL_PASS_MERGE_SRC);
+      const float2 jv = SRC ? s_t0[Cfg::sidx(k, c)] : make_float2(0.f, 0.f);
+      const float2 jp = (SRC && packed) ? s_t0[Cfg::sidx(neg_mod<L>(k), c)] : make_float2(0.f, 0.f);
+      v[m] = merged_mode<SRC>(v[m], packed ? vp[m] : v[m], eg, packed ? egn[m] : eg, off0, Tl, packed, jv, jp);
     } else if constexpr (MODE == COL_PASS_2DF) {
       const float2 t0o = s_t0[k * W + c];
       float2 t0n, d0;

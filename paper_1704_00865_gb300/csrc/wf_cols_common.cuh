@@ -37,6 +37,40 @@ __device__ __forceinline__ float2 mode_2df(float2 yv, float2 t0o, float C, float
   return d0;
 }
 
+// The merged 2DF block given the data-side messenger y, one mode (Appendix A
+// shortcut): d_2DF = (C + N0)/(C + N0 + T) y, s = C/(C + N0) d_2DF implicit.
+// With a source j in the objective (-2 s.j, defect correction) the joint
+// minimiser is d_2DF = ((C + N0) y + T C j^) / (C + N0 + T).  For the packed
+// column 0 (kx = 0 and kx = nx/2 as one complex column) the partner values
+// at -ky (vp, jp) and the kx = nx/2 eigenvalues egb enter as well.
+template <bool SRC>
+__device__ __forceinline__ float2 merged_mode(float2 v, float2 vp, float2 eg, float2 egb, float off0, float Tl,
+                                              bool packed, float2 jv, float2 jp) {
+  const float pa = eg.x + eg.y + off0;
+  if constexpr (!SRC) {
+    if (packed) {
+      const float pb = egb.x + egb.y + off0;
+      float2 A, B;
+      unpack_pair(v, vp, A, B);
+      return repack_pair(cscale(A, __fdividef(pa, pa + Tl)), cscale(B, __fdividef(pb, pb + Tl)));
+    }
+    return cscale(v, __fdividef(pa, pa + Tl));
+  } else {
+    if (packed) {
+      const float pb = egb.x + egb.y + off0;
+      float2 A, B, JA, JB;
+      unpack_pair(v, vp, A, B);
+      unpack_pair(jv, jp, JA, JB);
+      const float ia = __fdividef(1.f, pa + Tl), ib = __fdividef(1.f, pb + Tl);
+      const float2 dA = make_float2((pa * A.x + Tl * eg.x * JA.x) * ia, (pa * A.y + Tl * eg.x * JA.y) * ia);
+      const float2 dB = make_float2((pb * B.x + Tl * egb.x * JB.x) * ib, (pb * B.y + Tl * egb.x * JB.y) * ib);
+      return repack_pair(dA, dB);
+    }
+    const float ia = __fdividef(1.f, pa + Tl);
+    return make_float2((pa * v.x + Tl * eg.x * jv.x) * ia, (pa * v.y + Tl * eg.x * jv.y) * ia);
+  }
+}
+
 // The column pass for one column length (wf_colpass.cu): modes COL_PASS_*.
 template <int L>
 int launch_col_pass_any(int mode, const ColArgs& a, cudaStream_t s);

@@ -151,6 +151,30 @@ bool col_tc_supported(int L);
 int row_pass_e(int M, int variant);
 int col_pass_e(int L, int variant);
 
+// The whole sweep, nsweeps times, in one cooperative launch (wf_fused.cu):
+// 1024 x 1024 maps with a stripe part and the merged 2DF block.
+struct FusedArgs {
+  int ny, nx;
+  int nsweeps;
+  const float4* dn;           // pixel table
+  float2* f_d1;               // d_RF, row-major RF
+  float2* f_t1;               // t_RF, column-tiled RF
+  float2* f_x;                // d_2DF, column-tiled RF
+  const float2* eig;          // (C, P1f), column-tiled
+  const float2* eig_nyq;      // (C, P1f) at kx = nx/2
+  const float* pst;           // stripe eigenvalues
+  const float* a2;            // a(y)^2 or nullptr
+  const float2* twx;          // exp(-2 pi i k/nx)
+  const float2* twh;          // exp(-2 pi i k/(nx/2))
+  const float2* twy;          // exp(-2 pi i k/ny)
+  const float2* src;          // 2D-Fourier source j^, column-tiled (src = 1)
+  WfState* st;
+  unsigned* bar;              // grid barrier words: arrivals, generation, abort
+};
+int launch_fused(const FusedArgs& a, cudaStream_t s);
+// whether the one-launch sweep handles this plan on the current device
+bool fused_supported(int ny, int nx, int has_rf, int merged, int prec);
+
 // setup / control kernels
 struct SetupArgs {
   int ny, nx;

@@ -12,6 +12,7 @@
 
 #include "wf_device.cuh"
 #include "wf_internal.h"
+#include "wf_rows_common.cuh"
 
 namespace wf {
 
@@ -38,12 +39,6 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
     for (int i = 0; i < NW; ++i) s += red[i];
   }
   return s;
-}
-
-// t_PX update for one pixel: links Nbar_PX to d and T_PX to u (the field on
-// the signal side); masked pixels (nb < 0, i.e. Nbar = inf) take u.
-__device__ __forceinline__ float tpx_update(float d, float nb, float u, float T2) {
-  return nb < 0.f ? u : __fdividef(fmaf(T2, d, nb * u), nb + T2);
 }
 
 template <int M, int MODE>
@@ -363,19 +358,7 @@ row_pass_kernel(RowArgs a) {
       const float2 xo = s_x[g * M + k];
       const float2 t2 = v[m];
       float2 d1, t1;
-      if (k == 0) {  // packed (kx = 0, kx = M) real pair
-        const float nr = fmaf(a2y, pk[0], off1), ni = fmaf(a2y, pkn, off1);
-        d1.x = __fdividef(fmaf(nr, t2.x, T2 * t1o.x), nr + T2);
-        d1.y = __fdividef(fmaf(ni, t2.y, T2 * t1o.y), ni + T2);
-        t1.x = __fdividef(fmaf(T1, d1.x, nr * xo.x), nr + T1);
-        t1.y = __fdividef(fmaf(T1, d1.y, ni * xo.y), ni + T1);
-      } else {
-        const float nb = fmaf(a2y, pk[m], off1);
-        const float wa = __fdividef(nb, nb + T2);      // weight of t_PX
-        d1 = make_float2(fmaf(wa, t2.x - t1o.x, t1o.x), fmaf(wa, t2.y - t1o.y, t1o.y));
-        const float wb = __fdividef(nb, nb + T1);      // weight of x
-        t1 = make_float2(fmaf(wb, xo.x - d1.x, d1.x), fmaf(wb, xo.y - d1.y, d1.y));
-      }
+      stripe_update(k, t2, t1o, xo, a2y, pk[m], pkn, off1, T2, T1, d1, t1);
       a.f_d1[row0 + k] = d1;
       a.f_t1[tidx(y, k, a.ny)] = t1;
     }

@@ -42,7 +42,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_host_only_entry_points(lib):
     from paper_1704_00865_gb300 import wf
-    assert lib.wf_version() == 1
+    assert lib.wf_version() == 2
     assert wf.strerror(0) == "ok"
     assert "converge" in wf.strerror(3)
     p = wf.wf_params_default()
@@ -51,7 +51,7 @@ def test_host_only_entry_points(lib):
     assert p.residual_every == 10 and p.check_every == 8
     assert p.merge_2df == 1 and p.tol_u_scale == 1.0 and p.refine == 0 and p.refine_tol_scale == 100.0
     assert p.autotune == 1 and p.stall_checks == 0 and p.refine_max_iters == 0
-    assert p.dft_precision == 0 and p.refine_extra == 0
+    assert p.dft_precision == 0 and p.refine_extra == 0 and p.sweep_kernel == 0
     assert lib.wf_plan_shapes(None, None, None) == wf.WF_EINVAL
 
 
@@ -103,12 +103,36 @@ def test_product_path_never_imports_the_oracle():
                 assert "wf_oracle" not in src, f
 
 
-def test_schedule_struct_layout_matches_header(lib):
+def test_schedule_struct_layout_matches_header(lib, tmp_path):
+    # the binding's ctypes structs against the C compiler's layout of the
+    # structs include/wf.h declares: every field's offset and the size
+    import shutil
+    import subprocess
     from paper_1704_00865_gb300 import wf
-    # int, ptr, ptr, int, 4 doubles on LP64
-    assert C.sizeof(wf.wf_schedule) == 4 + 4 + 8 + 8 + 4 + 4 + 32
-    assert C.sizeof(wf.wf_params) == 24 + 24 + 8 + 16 + 8 + 8 + 8 + 8 + 8
-    assert C.sizeof(wf.wf_stats) == 8 + 8 * 3 + 24 + 8
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    structs = [wf.wf_schedule, wf.wf_params, wf.wf_stats, wf.wf_map]
+    lines = []
+    for st in structs:
+        name = st.__name__
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for f, _ in st._fields_:
+            lines.append(f'printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    src = tmp_path / "layout.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "wf.h"\nint main(void) {\n' +
+                   "\n".join(lines) + "\nreturn 0;\n}\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], capture_output=True,
+                       text=True)
+    assert r.returncode == 0, r.stderr
+    got = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split("\n")
+               if l)
+    for st in structs:
+        name = st.__name__
+        assert int(got[name]) == C.sizeof(st), name
+        for f, _ in st._fields_:
+            assert int(got[f"{name}.{f}"]) == getattr(st, f).offset, (name, f)
 
 
 @pytest.mark.parametrize("sizes,lanes,parts,code", [
