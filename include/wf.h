@@ -190,17 +190,19 @@ typedef struct {
  *                  ny in {512, 1024, 2048, 4096} and merge_2df = 1
  *                  (WF_EUNSUPPORTED otherwise); the column shape is then the
  *                  16-value one.
- *  sweep_kernel    how a sweep is launched: 0 (default) as one cooperative
- *                  launch per residual_every sweeps where the plan allows it
+ *  sweep_kernel    how sweeps are launched: 0 (default) a row-pass and a
+ *                  column-pass launch per sweep; 1 one cooperative launch
+ *                  per residual_every sweeps, the passes separated by grid
+ *                  barriers, every CTA keeping the tables and fields of its
+ *                  own rows and column tile in shared memory across sweeps
  *                  (1024 x 1024 maps with a stripe part, the merged 2DF block
  *                  or no 1/f part, dft_precision 0, a GPU with at least 128
- *                  SMs), else as a row-pass and a column-pass launch per
- *                  sweep; 1 always the two launches; 2 always one launch
- *                  (WF_EUNSUPPORTED from wf_plan_create where it cannot).
- *                  In the one-launch form every CTA keeps the tables and
- *                  fields of its own rows and column tile in shared memory
- *                  across sweeps; the arithmetic is that of the two
- *                  launches, with 8 values per thread in both transforms.
+ *                  SMs; WF_EUNSUPPORTED from wf_plan_create otherwise).  The
+ *                  arithmetic is that of the two launches, with 8 values per
+ *                  thread in both transforms.  On a GB300 the one-launch
+ *                  form measured slower at 1024^2 (its two grid barriers cost
+ *                  more than the launch boundaries they replace), so it is
+ *                  not the default.
  */
 typedef struct {
   double theta[3];

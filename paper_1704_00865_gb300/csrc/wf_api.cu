@@ -212,7 +212,7 @@ int wf::check_plan_args(int ny, int nx, unsigned parts, const wf_params* p) {
   if (prm.refine < 0 || prm.refine > 8 || !(prm.refine_tol_scale >= 1.0) || prm.refine_max_iters < 0 ||
       prm.refine_lam1_iters < 0 || prm.stall_checks < 0 || prm.autotune < 0 || prm.autotune > 2 ||
       prm.refine_extra < 0 || prm.refine_extra > 8 ||
-      prm.dft_precision < 0 || prm.dft_precision > 2 || prm.sweep_kernel < 0 || prm.sweep_kernel > 2)
+      prm.dft_precision < 0 || prm.dft_precision > 2 || prm.sweep_kernel < 0 || prm.sweep_kernel > 1)
     return WF_EINVAL;
   // tensor-core radix-16 stages: 16-value column shapes, merged 2DF block
   if (prm.dft_precision != 0 && (!col_tc_supported(ny) || prm.merge_2df != 1)) return WF_EUNSUPPORTED;
@@ -309,10 +309,10 @@ int wf_plan_create(wf_plan_t* out, int ny, int nx, unsigned parts, const wf_para
     wf_plan_destroy(P);
     return WF_ECUDA;
   }
-  // one launch per R sweeps where the map fits it (or when asked to)
-  if (prm.sweep_kernel != 1) {
+  // one cooperative launch per R sweeps, when asked for
+  if (prm.sweep_kernel == 1) {
     P->fused = fused_supported(ny, nx, P->has_rf, P->merge || !P->has_f, prm.dft_precision);
-    if (!P->fused && prm.sweep_kernel == 2) {
+    if (!P->fused) {
       wf_plan_destroy(P);
       return WF_EUNSUPPORTED;
     }
@@ -441,6 +441,7 @@ static int enqueue_sweeps(wf_plan_s* P, int n, long long first) {
   f.src = P->has_src ? P->src_2df : nullptr;
   f.st = P->st;
   f.bar = P->fbar;
+  CK(cudaMemsetAsync(P->fbar, 0, sizeof(unsigned), P->stream));  // the arrival count
   CKI(launch_fused(f, P->stream));
   P->launches += 1;
   return WF_OK;

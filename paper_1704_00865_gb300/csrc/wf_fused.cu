@@ -21,10 +21,10 @@
 // own (wf_device.cuh, wf_rows_common.cuh, wf_cols_common.cuh), with 8 values
 // per thread in both transforms.
 //
-// The grid barrier counts arrivals on a global word and releases waiters by
-// bumping a generation word; its waits are bounded, and a CTA that gives up
-// raises an abort word that ends every other wait, records WF_ERR_TIMEOUT
-// and returns.  The cooperative launch guarantees that all 128 CTAs are
+// The grid barrier counts arrivals on a global word that is zeroed before
+// each launch; its waits are bounded, and a CTA that gives up raises an
+// abort word that ends every other wait, records WF_ERR_TIMEOUT and
+// returns.  The cooperative launch guarantees that all 128 CTAs are
 // resident at once (it fails instead of starting otherwise).
 #include <cuda_runtime.h>
 
@@ -84,38 +84,34 @@ __device__ __forceinline__ unsigned ld_relaxed_gpu(const unsigned* p) {
   return v;
 }
 
-// Waits this many polls at most (each a global load and a short sleep); a
-// sweep's barrier normally waits a few microseconds.
+// Waits this many polls at most (each a global load, about half a
+// microsecond); a sweep's barrier normally waits one or two microseconds.
 constexpr int WF_GRID_TRIES = 1 << 21;
 
-// All CTAs of the grid meet here.  bar[0] counts arrivals, bar[1] is the
-// generation (the last arrival resets the count and bumps it), bar[2] is the
-// abort word.  `gen` (thread 0 only) is the generation this CTA waits to
-// leave.  Returns false, for every thread of the CTA, if the wait gave up or
+// All CTAs of the grid meet here.  bar[0] counts the arrivals of this launch
+// (zeroed before it starts); the k-th barrier of the launch is passed once
+// it reaches k * nblocks.  Each arrival is an acquire-release add (the CTA's
+// writes, ordered before it by the block barrier, are released; the last
+// arrival need not wait for a second word to change), and the waits are
+// acquire loads of the same word, so one round trip to L2 separates the
+// last arrival from the others' release.  bar[2] is the abort word.
+// Returns false, for every thread of the CTA, if the wait gave up or
 // another CTA aborted.
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned& gen, int* ok_s,
-                                             unsigned* err) {
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned target, int* ok_s, unsigned* err) {
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    __threadfence();
-    if (atomicAdd(&bar[0], 1u) == nblocks - 1) {
-      bar[0] = 0u;  // every other CTA is waiting on the generation word
-      __threadfence();
-      atomicAdd(&bar[1], 1u);
-    } else {
-      for (int i = 0; ld_acquire_gpu(&bar[1]) == gen; ++i) {
-        if (i >= WF_GRID_TRIES || ld_relaxed_gpu(&bar[2]) != 0u) {
-          atomicExch(&bar[2], 1u);
-          atomicOr(err, WF_ERR_TIMEOUT);
-          ok = 0;
-          break;
-        }
-        __nanosleep(64);
+    unsigned seen;
+    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(seen) : "l"(bar) : "memory");
+    for (int i = 0; seen + 1u < target; ++i) {
+      if (i >= WF_GRID_TRIES || ld_relaxed_gpu(&bar[2]) != 0u) {
+        atomicExch(&bar[2], 1u);
+        atomicOr(err, WF_ERR_TIMEOUT);
+        ok = 0;
+        break;
       }
+      seen = ld_acquire_gpu(bar) - 1u;
     }
-    __threadfence();
-    gen += 1u;
     *ok_s = ok;
   }
   __syncthreads();
@@ -187,8 +183,7 @@ fused_sweep_kernel(FusedArgs a) {
   const float a2y = (a.a2 != nullptr) ? __ldg(&a.a2[y]) : 1.f;
   const float T2 = a.st->Tf[2], T1 = a.st->Tf[1];
   const float off1 = (float)a.st->off[1], off0 = (float)a.st->off[0];
-  unsigned gen = 0;
-  if (tid == 0) gen = ld_acquire_gpu(&a.bar[1]);  // before this CTA's first arrival
+  unsigned nbar = 0;  // barriers passed in this launch
   const bool ok0 = mbar_wait(&mbar[0], 0, WF_WAIT_TRIES);
   cp_async_wait<0>();
   if (__syncthreads_or(!ok0)) {
@@ -235,7 +230,7 @@ fused_sweep_kernel(FusedArgs a) {
       for (int i = tid; i < L * W / 2; i += NT) cp_async16(s_src + 2 * i, a.src + tile0 + 2 * i);
       cp_async_commit();
     }
-    if (!grid_barrier(a.bar, gridDim.x, gen, ok_s, &a.st->err)) {
+    if (!grid_barrier(a.bar, ++nbar * gridDim.x, ok_s, &a.st->err)) {
       cp_async_wait<0>();
       return;
     }
@@ -272,7 +267,7 @@ fused_sweep_kernel(FusedArgs a) {
 #pragma unroll
     for (int m = 0; m < CE; ++m) a.f_x[tile0 + (size_t)(tc + m * TPC) * W + c] = cscale(u[m], sc);
     // the next row pass reads d_2DF of every tile (none after the last sweep)
-    if (it + 1 < a.nsweeps && !grid_barrier(a.bar, gridDim.x, gen, ok_s, &a.st->err)) return;
+    if (it + 1 < a.nsweeps && !grid_barrier(a.bar, ++nbar * gridDim.x, ok_s, &a.st->err)) return;
   }
   // d_RF of this CTA's rows back to global memory
   __syncthreads();

@@ -169,7 +169,7 @@ struct FusedArgs {
   const float2* twy;          // exp(-2 pi i k/ny)
   const float2* src;          // 2D-Fourier source j^, column-tiled (src = 1)
   WfState* st;
-  unsigned* bar;              // grid barrier words: arrivals, generation, abort
+  unsigned* bar;              // grid barrier words: arrivals (zeroed before each launch), -, abort
 };
 int launch_fused(const FusedArgs& a, cudaStream_t s);
 // whether the one-launch sweep handles this plan on the current device

@@ -107,3 +107,35 @@ def test_radix3_sizes_converge_to_closed_form(wf, n):
     print(f"{n}^2 homogeneous: {st['iters']} iterations, rel L2 vs closed form {err:.2e}")
     assert st["status"] == 0, st
     assert err < 1e-4
+
+
+@pytest.mark.slow
+@pytest.mark.skipif(os.environ.get("WF_LONG_TESTS") != "1",
+                    reason="about 10 minutes of FP64 PCG on the host (set WF_LONG_TESTS=1)")
+def test_4096_three_part_masked_solve_against_pcg(wf):
+    # the largest map with the benchmark's noise model, mask, solver settings
+    # and stop test: rel L2 against the FP64 PCG solution (eq. wiener-alt),
+    # over all pixels and over the masked pixels alone, and the literal
+    # residual the oracle measures by CG
+    import torch
+    import bench
+    n = 4096
+    prob = synth.cfg1_problem(3000, n)
+    P = O.build_parts(prob)
+    plan = wf.Plan(n, n, wf.parts_of(prob), bench.solver_params(wf))
+    out = torch.empty(n, n, device="cuda")
+    dv = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    _, st = plan.solve(*[dv(a) for a in (prob.d, prob.pixel_var, prob.mask, prob.C, prob.P1f, prob.Pst,
+                                         prob.stripe_amp2)], bench.solver_schedule(wf), bench.TOL, out=out)
+    plan.close()
+    s = out.cpu().numpy().astype(np.float64)
+    s_ref = O.pcg_wf(prob, P=P, tol=1e-10)
+    lit = O.literal_residual(prob, s, P=P, tol=1e-10)
+    m = prob.mask.astype(bool)
+    err, err_m = rel(s, s_ref), rel(s[m], s_ref[m])
+    print(f"4096^2 solve: {st['iters']} sweeps, status {st['status']}, literal residual {lit:.2e}, "
+          f"rel L2 {err:.2e} (masked pixels {err_m:.2e})")
+    assert st["status"] == 0, st
+    assert lit < 1e-5, lit
+    assert err < 1e-4, err
+    assert err_m < 1e-4, err_m
