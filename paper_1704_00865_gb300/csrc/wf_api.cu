@@ -1190,8 +1190,12 @@ int wf_time_passes(wf_plan_t P, double lam, int n, double* us_row, double* us_co
   if (!P || !P->loaded || n < 1 || !(lam >= 1.0) || !isfinite(lam)) return WF_EINVAL;
   // n launches of one pass captured back to back in a graph on the plan's
   // stream, timed by events around the replay: the per-launch time without
-  // host launch overhead
+  // host launch overhead.  The plan's stream starts after the work already
+  // queued on the caller's stream (earlier iterations must not overlap the
+  // timed replays).
   cudaStream_t user = P->stream;
+  CK(cudaEventRecord(P->ev_in, user));
+  CK(cudaStreamWaitEvent(P->gstream, P->ev_in, 0));
   P->stream = P->gstream;
   int rc = WF_OK;
   double res[2] = {0.0, 0.0};
@@ -1242,8 +1246,11 @@ int wf_time_sweeps(wf_plan_t P, double lam, int n, double* us_per_sweep, int* on
   if (!P || !P->loaded || n < 1 || !(lam >= 1.0) || !isfinite(lam)) return WF_EINVAL;
   // n sweeps as the plan's iteration runs them (one cooperative launch, or
   // n row-pass / column-pass pairs), captured in a graph on the plan's
-  // stream and timed by events around its replay
+  // stream and timed by events around its replay, after the work already
+  // queued on the caller's stream
   cudaStream_t user = P->stream;
+  CK(cudaEventRecord(P->ev_in, user));
+  CK(cudaStreamWaitEvent(P->gstream, P->ev_in, 0));
   P->stream = P->gstream;
   int rc = WF_OK;
   float ms = 0.f;
