@@ -527,7 +527,7 @@ def run_batch(args):
     sched = solver_schedule(wf)
     stream = torch.cuda.current_stream()
     res = {}
-    for name, lanes in (("plain", 1), ("batched", BATCH_LANES)):
+    for name, lanes in (("plain", 1), ("batched", BATCH_LANES), ("persistent", 0)):
         b = wf.Batch(shapes, params=solver_params(wf), lanes=lanes)
         for _ in range(max(args.warmup, 0)):
             b.solve(inputs, sched, TOL, outs)
@@ -558,6 +558,10 @@ def run_batch(args):
             "plain": {"solves_per_s": round(res["plain"]["solves_per_s"], 4),
                       "ms_per_batch": round(res["plain"]["ms_per_batch"], 3)},
             "speedup_vs_plain": round(res["batched"]["solves_per_s"] / res["plain"]["solves_per_s"], 3),
+            "persistent": {k: (round(v, 4) if isinstance(v, float) else v) for k, v in res["persistent"].items()
+                           if k != "iters"},
+            "persistent_speedup_vs_plain": round(res["persistent"]["solves_per_s"] / res["plain"]["solves_per_s"], 3),
+            "persistent_iters_per_map": res["persistent"]["iters"],
             "iters_per_map": res["batched"]["iters"], "status": res["batched"]["status"],
             "maps_passing_stop_test": res["batched"]["ok"],
             "worst_rel_rho_u": res["batched"]["worst_u"], "worst_rel_rho_m": res["batched"]["worst_m"],

@@ -427,11 +427,14 @@ WF_API int wf_fft2_noalloc(int ny, int nx, const float* in, float* out,
 
 /* ------------------------------------------------------------------------
  * Batched solves: many independent maps of uneven sizes (the parts and
- * parameters shared).  Every map gets its own plan; the maps are spread over
- * `lanes` host worker threads, each driving its maps one after another on
- * its own CUDA stream, so up to `lanes` solves share the GPU at once (small
- * maps fill only a few SMs each).  A map's result is the one wf_solve gives
- * for it alone: same kernels, same order, bit for bit.
+ * parameters shared).  Every map gets its own plan.  With lanes > 0 the maps
+ * are spread over `lanes` host worker threads, each driving its maps one
+ * after another on its own CUDA stream, so up to `lanes` solves share the GPU
+ * at once (small maps fill only a few SMs each); a map's result is then the
+ * one wf_solve gives for it alone, bit for bit.  With lanes = 0 the maps'
+ * iterations run together in persistent launches (see wf_batch_create); the
+ * steps of each map's solve are those of wf_solve, its transforms may take
+ * other shapes (rounding order only).
  * ------------------------------------------------------------------------ */
 
 typedef struct wf_batch_s* wf_batch_t;
@@ -456,7 +459,20 @@ typedef struct {
  *   parts   as for wf_plan_create, shared by all maps
  *   p       parameters (NULL: defaults), shared
  *   lanes   concurrent solves (host threads and streams), 1 .. 64; maps go
- *           to lanes largest first, each to the lane with the fewest pixels
+ *           to lanes largest first, each to the lane with the fewest pixels.
+ *           0: persistent mode -- the sweeps of all maps run together in
+ *           one persistent cooperative launch per residual checkpoint, with
+ *           device work queues over (map, row group) and (map, column group)
+ *           items, a grid barrier between the row and column phases and
+ *           per-map done flags (each map keeps its own lambda, residual and
+ *           stop test); every polling chunk of checkpoints, with each map's
+ *           residual and controller kernels, is one CUDA graph.  Maps must
+ *           be square with sides 256, 384, 512, 768, 1024, 1536 or 2048,
+ *           with a stripe part and the merged 2DF block (or no 1/f part),
+ *           dft_precision 0 (WF_EUNSUPPORTED otherwise).  Each size has one
+ *           or two compiled shapes of its transforms; wf_params.autotune
+ *           picks them as for a plan (1: timed on the first map of the size,
+ *           cached per size and device for the process).
  *   stream  the caller's stream: wf_batch_solve starts after the work
  *           already on it and the caller's later work waits for the batch
  * Allocates every plan's workspace up front (about 14 maps of 4 ny nx bytes

@@ -696,7 +696,251 @@ static void fill_stats(wf_plan_s* P, wf_stats* st, int status) {
   st->parts = (int)P->parts;
 }
 
-static int wf_run_on(wf_plan_t P, const wf_schedule* sch, double tol, wf_stats* st) {
+}  // extern "C"
+
+// ---------------------------------------------------------------- persistent batch
+static int run_setup(wf_plan_t P, const wf_schedule* sch, double tol, CtrlArgs* out, double* lam0_out);
+
+// The map's fields and tables as the persistent batch kernel takes them
+// (merged 2DF block with a stripe part, square maps of the batch sizes).
+int wf::plan_batch_map(wf_plan_t P, int variant, BatchMapArgs* out) {
+  if (!P || P->ny != P->nx || !P->has_rf || (P->has_f && !P->merge) || P->p.dft_precision != 0) return WF_EUNSUPPORTED;
+  const int cls = batch_class(P->ny, variant);
+  if (cls < 0) return WF_EUNSUPPORTED;
+  BatchMapArgs m{};
+  m.cls = cls;
+  m.dn = P->dn;
+  m.f_d1 = P->f_d1;
+  m.f_t1 = P->f_t1;
+  m.f_x = P->f_x;
+  m.eig = P->eig;
+  m.eig_nyq = P->eig_nyq;
+  m.pst = P->pst;
+  m.a2 = P->a2;
+  m.twx = P->twx;
+  m.twh = P->twh;
+  m.twy = P->twy;
+  m.src = P->has_src ? P->src_2df : nullptr;
+  m.st = P->st;
+  *out = m;
+  return WF_OK;
+}
+
+bool wf::plan_batch_ok(const wf_plan_t P) {
+  return P && P->ny == P->nx && P->has_rf && !(P->has_f && !P->merge) && P->p.dft_precision == 0 &&
+         batch_class(P->ny, 0) >= 0;
+}
+
+int wf::plan_size(const wf_plan_t P) { return P->ny; }
+int wf::plan_autotune(const wf_plan_t P) { return P->p.autotune; }
+
+// Runs the iteration of several loaded plans together (wf_run for each, with
+// one schedule and stop tolerance): per checkpoint one persistent launch of
+// R sweeps for all of them (wf_batchk.cu), then each plan's residual and
+// controller; K checkpoints per CUDA graph, captured once and replayed on
+// `s` until every plan is done or at its cap.  status[i] and st[i] receive
+// what wf_run would return for plan i.
+int wf::run_plans_persistent(const std::vector<wf_plan_t>& plans, const std::vector<int>& variant,
+                             const wf_schedule* sch, double tol, BatchDevice& bd, cudaStream_t s,
+                             std::vector<int>& status, std::vector<wf_stats>& st) {
+  const size_t n = plans.size();
+  status.assign(n, WF_OK);
+  st.assign(n, wf_stats{});
+  if (n == 0) return WF_OK;
+  const int R = plans[0]->p.residual_every, K = plans[0]->p.check_every;
+  std::vector<CtrlArgs> ctrl(n);
+  std::vector<BatchMapArgs> maps(n);
+  std::vector<cudaStream_t> own(n);
+  long long cap = 0;
+  for (size_t i = 0; i < n; ++i) {
+    wf_plan_t P = plans[i];
+    own[i] = P->stream;
+    P->stream = s;
+    double lam0 = 1.0;
+    int rc = run_setup(P, sch, tol, &ctrl[i], &lam0);
+    if (!rc) rc = launch_set_lambda(P->st, lam0, 1, s) ? WF_ECUDA : WF_OK;
+    if (!rc) rc = plan_batch_map(P, variant[i], &maps[i]);
+    if (rc) {
+      for (size_t j = 0; j <= i; ++j) plans[j]->stream = own[j];
+      return rc;
+    }
+    P->launches += 1;
+    cap = std::max<long long>(cap, ctrl[i].max_iters);
+  }
+  // work queues: the largest maps first, so the small ones fill in at the end
+  std::vector<size_t> order(n);
+  for (size_t i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return plans[a]->ny > plans[b]->ny; });
+  bd.row_items.clear();
+  bd.col_items.clear();
+  for (size_t i : order) {
+    int rows = 0, cols = 0, re = 0, ce = 0;
+    batch_item_shape(maps[i].cls, &rows, &cols, &re, &ce);
+    for (int g = 0; g < plans[i]->ny / rows; ++g) bd.row_items.push_back(make_int2((int)i, g));
+    for (int g = 0; g < (plans[i]->nx / 2) / cols; ++g) bd.col_items.push_back(make_int2((int)i, g));
+  }
+  int rc = WF_OK;
+  auto restore = [&]() {
+    for (size_t i = 0; i < n; ++i) plans[i]->stream = own[i];
+  };
+  if (bd.row_items.size() > bd.cap_items || bd.col_items.size() > bd.cap_items || n > bd.cap_maps) {
+    restore();
+    return WF_EINVAL;
+  }
+  if (cudaMemcpyAsync(bd.maps, maps.data(), n * sizeof(BatchMapArgs), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(bd.rows, bd.row_items.data(), bd.row_items.size() * sizeof(int2), cudaMemcpyHostToDevice, s) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(bd.cols, bd.col_items.data(), bd.col_items.size() * sizeof(int2), cudaMemcpyHostToDevice, s) !=
+          cudaSuccess ||
+      cudaMemsetAsync(bd.err, 0, sizeof(unsigned), s) != cudaSuccess) {
+    cudaGetLastError();
+    restore();
+    return WF_ECUDA;
+  }
+  BatchArgs a{};
+  a.maps = bd.maps;
+  a.row_items = bd.rows;
+  a.col_items = bd.cols;
+  a.n_row = (int)bd.row_items.size();
+  a.n_col = (int)bd.col_items.size();
+  a.nsweeps = R;
+  a.bar = bd.bar;
+  a.queue = bd.queue;
+  a.err = bd.err;
+  long long launches_per_chunk = 0;
+  // one chunk: K checkpoints of one persistent launch and every plan's
+  // residual and controller
+  auto enqueue_chunk = [&]() -> int {
+    for (int cp = 0; cp < K; ++cp) {
+      if (cudaMemsetAsync(bd.bar, 0, 4 * sizeof(unsigned), s) != cudaSuccess ||
+          cudaMemsetAsync(bd.queue, 0, 2 * (size_t)R * sizeof(unsigned), s) != cudaSuccess)
+        return WF_ECUDA;
+      if (launch_batch_sweeps(a, bd.grid, s)) return WF_ECUDA;
+      launches_per_chunk += 1;
+      for (size_t i = 0; i < n; ++i) {
+        int r2 = enqueue_residual(plans[i], 0, 1);
+        if (r2) return r2;
+        if (launch_ctrl(ctrl[i], s)) return WF_ECUDA;
+        plans[i]->launches += 1;
+      }
+    }
+    return WF_OK;
+  };
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  const long long l0 = 0;
+  (void)l0;
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = WF_ECUDA;
+  if (!rc) {
+    std::vector<long long> before(n);
+    for (size_t i = 0; i < n; ++i) before[i] = plans[i]->launches;
+    rc = enqueue_chunk();
+    cudaError_t ce = cudaStreamEndCapture(s, &g);
+    if (!rc && (ce != cudaSuccess || cudaGraphInstantiate(&ge, g, 0) != cudaSuccess)) rc = WF_ECUDA;
+    // launches are counted per replay below
+    for (size_t i = 0; i < n; ++i) bd.per_plan_launches = plans[i]->launches - before[i];
+    for (size_t i = 0; i < n; ++i) plans[i]->launches = before[i];
+  }
+  long long enq = 0;
+  std::vector<WfState> hst(n);
+  while (!rc) {
+    if (cudaGraphLaunch(ge, s) != cudaSuccess) {
+      rc = WF_ECUDA;
+      break;
+    }
+    bd.launches += launches_per_chunk;
+    for (size_t i = 0; i < n; ++i) plans[i]->launches += bd.per_plan_launches;
+    enq += (long long)K * R;
+    for (size_t i = 0; i < n && !rc; ++i)
+      if (cudaMemcpyAsync(plans[i]->h_st, plans[i]->st, sizeof(WfState), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        rc = WF_ECUDA;
+    if (!rc && cudaStreamSynchronize(s) != cudaSuccess) rc = WF_ECUDA;
+    if (rc) break;
+    bool all = true;
+    for (size_t i = 0; i < n; ++i) all = all && plans[i]->h_st->done;
+    if (all || enq >= cap) break;
+  }
+  if (ge) cudaGraphExecDestroy(ge);
+  if (g) cudaGraphDestroy(g);
+  unsigned err = 0;
+  if (!rc && cudaMemcpy(&err, bd.err, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) rc = WF_ECUDA;
+  restore();
+  if (rc) {
+    cudaGetLastError();
+    return rc;
+  }
+  for (size_t i = 0; i < n; ++i) {
+    wf_plan_t P = plans[i];
+    P->it_done = P->h_st->iter;
+    if ((P->h_st->err & WF_ERR_TIMEOUT) || (err & WF_ERR_TIMEOUT)) {
+      status[i] = WF_ETIMEOUT;
+      continue;
+    }
+    const int hs = P->h_st->status;
+    status[i] = hs == 3 ? WF_ENOCONV : (hs == 4 ? WF_ESTALL : WF_OK);
+    fill_stats(P, &st[i], status[i]);
+  }
+  return WF_OK;
+}
+
+// Mean time of one sweep of plan P alone in the persistent batch kernel with
+// shape `variant` (the batch's tuner; overwrites P's fields and state).
+int wf::time_batch_variant(wf_plan_t P, int variant, BatchDevice& bd, cudaStream_t s, double* us) {
+  BatchMapArgs m{};
+  int rc = plan_batch_map(P, variant, &m);
+  if (rc) return rc;
+  const int ns = std::max(1, std::min(4, P->p.residual_every));
+  int rows = 0, cols = 0, re = 0, ce = 0;
+  batch_item_shape(m.cls, &rows, &cols, &re, &ce);
+  bd.row_items.clear();
+  bd.col_items.clear();
+  for (int g = 0; g < P->ny / rows; ++g) bd.row_items.push_back(make_int2(0, g));
+  for (int g = 0; g < (P->nx / 2) / cols; ++g) bd.col_items.push_back(make_int2(0, g));
+  BatchArgs a{};
+  a.maps = bd.maps;
+  a.row_items = bd.rows;
+  a.col_items = bd.cols;
+  a.n_row = (int)bd.row_items.size();
+  a.n_col = (int)bd.col_items.size();
+  a.nsweeps = ns;
+  a.bar = bd.bar;
+  a.queue = bd.queue;
+  a.err = bd.err;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  float ms = 0.f;
+  rc = WF_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
+      launch_set_lambda(P->st, 1.0, 1, s) ||
+      cudaMemcpyAsync(bd.maps, &m, sizeof(m), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaMemcpyAsync(bd.rows, bd.row_items.data(), bd.row_items.size() * sizeof(int2), cudaMemcpyHostToDevice, s) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(bd.cols, bd.col_items.data(), bd.col_items.size() * sizeof(int2), cudaMemcpyHostToDevice, s) !=
+          cudaSuccess)
+    rc = WF_ECUDA;
+  for (int rep = 0; rep < 2 && !rc; ++rep) {
+    if (cudaMemsetAsync(bd.bar, 0, 4 * sizeof(unsigned), s) != cudaSuccess ||
+        cudaMemsetAsync(bd.queue, 0, 2 * (size_t)ns * sizeof(unsigned), s) != cudaSuccess ||
+        cudaEventRecord(e0, s) != cudaSuccess || launch_batch_sweeps(a, bd.grid, s) ||
+        cudaEventRecord(e1, s) != cudaSuccess)
+      rc = WF_ECUDA;
+  }
+  if (!rc && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)) rc = WF_ECUDA;
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (rc) {
+    cudaGetLastError();
+    return rc;
+  }
+  P->launches += 3;
+  P->loaded = false;
+  *us = 1000.0 * ms / ns;
+  return WF_OK;
+}
+
+// Controller arguments and device schedule of a run (wf_run and the
+// persistent batch): validates the schedule, uploads a fixed schedule's
+// levels to the plan, and gives the first lambda.
+static int run_setup(wf_plan_t P, const wf_schedule* sch, double tol, CtrlArgs* out, double* lam0_out) {
   const int R = P->p.residual_every;
   CtrlArgs c = ctrl_args(P);
   c.tol = tol;
@@ -732,6 +976,19 @@ static int wf_run_on(wf_plan_t P, const wf_schedule* sch, double tol, wf_stats* 
   } else {
     return WF_EINVAL;
   }
+  *out = c;
+  *lam0_out = lam0;
+  return WF_OK;
+}
+
+extern "C" {
+
+static int wf_run_on(wf_plan_t P, const wf_schedule* sch, double tol, wf_stats* st) {
+  const int R = P->p.residual_every;
+  CtrlArgs c;
+  double lam0;
+  int rc0 = run_setup(P, sch, tol, &c, &lam0);
+  if (rc0) return rc0;
   CKI(launch_set_lambda(P->st, lam0, 1, P->stream));
   P->launches += 1;
   const long long it0 = P->it_done;
@@ -962,139 +1219,208 @@ static int warm_init(wf_plan_s* P, const float* s_init) {
   return WF_OK;
 }
 
-static int solve_impl(wf_plan_t P, const float* d, const float* pixel_var, const uint8_t* mask, const float* C,
-                      const float* P1f, const float* Pst, const float* stripe_amp2, const float* s_init,
-                      const wf_schedule* sched, double tol, float* s_out, wf_stats* st) {
-  if (!P || !s_out || !sched) return WF_EINVAL;
-  if (ptr_where(s_out) == PTR_OTHER_DEVICE) return WF_EINVAL;
+// One wf_solve as a sequence of steps: load the problem, the first run,
+// then the defect-correction solves (each a preparation, a run and a
+// subtraction), the residual of the refined s, and the output.  wf_solve
+// takes the steps in order with wf_run between them; a persistent batch
+// (wf_batch.cu) takes each step for all its maps and runs their iterations
+// together.
+static bool finished_rc(int r) { return r == WF_OK || r == WF_ENOCONV || r == WF_ESTALL; }
+
+int wf::job_start(SolveJob& J, const float* d, const float* pixel_var, const uint8_t* mask, const float* C,
+                  const float* P1f, const float* Pst, const float* stripe_amp2, const float* s_init) {
+  wf_plan_t P = J.P;
+  if (!P || !J.s_out || !J.sched) return WF_EINVAL;
+  if (ptr_where(J.s_out) == PTR_OTHER_DEVICE) return WF_EINVAL;
   int rc = wf_set_problem(P, d, pixel_var, mask, C, P1f, Pst, stripe_amp2);
   if (rc) return rc;
   if (s_init && (rc = warm_init(P, s_init))) return rc;
-  wf_stats s0{};
-  int status = wf_run(P, sched, tol, &s0);
-  auto finished = [](int r) { return r == WF_OK || r == WF_ENOCONV || r == WF_ESTALL; };
-  if (!finished(status)) return status;
+  return WF_OK;
+}
+
+int wf::job_after_first(SolveJob& J, int run_status, const wf_stats& s0, bool* done) {
+  wf_plan_t P = J.P;
+  *done = true;
+  J.status = run_status;
+  if (!finished_rc(run_status)) return run_status;
   if (P->p.refine == 0) {
-    rc = wf_get_field(P, WF_FIELD_S, s_out);
+    int rc = wf_get_field(P, WF_FIELD_S, J.s_out);
     if (rc) return rc;
-    if (st) *st = s0;
-    return status;
+    if (J.st) *J.st = s0;
+    return WF_OK;
   }
   // defect correction: s <- s - WF(Delta d_u(s)), Delta d against the original d
   const size_t npx = (size_t)P->ny * P->nx;
-  const double du2 = P->h_st->du2;
+  J.du2 = P->h_st->du2;
   CK(cudaMemcpyAsync(P->dn_orig, P->dn, npx / 2 * sizeof(float4), cudaMemcpyDeviceToDevice, P->stream));
-  if ((rc = wf_get_field(P, WF_FIELD_S, P->s_acc))) return rc;
-  wf_stats tot = s0;
-  const size_t nhb = (size_t)P->ny * P->M * sizeof(float2);
+  int rc = wf_get_field(P, WF_FIELD_S, P->s_acc);
+  if (rc) return rc;
+  J.tot = s0;
   // a source on masked pixels needs the merged 2DF block (or no 1/f part)
-  const bool with_src = !(P->has_f && !P->merge);
+  J.with_src = !(P->has_f && !P->merge);
   // A capped correction runs the fixed schedule's levels for at most
   // refine_max_iters - refine_lam1_iters sweeps, then lambda = 1 for the
   // rest: the cooling levels move the slow modes, the lambda = 1 sweeps
   // remove the bias the last level leaves in the fast ones.
-  wf_schedule csched = *sched;
-  std::vector<double> clam;
-  std::vector<int> citers;
+  const wf_schedule* sched = J.sched;
+  J.csched = *sched;
+  J.clam.clear();
+  J.citers.clear();
   const int cap = P->p.refine_max_iters;
   if (cap > 0 && sched->mode == WF_SCHED_FIXED && sched->lam && sched->iters && sched->nlevels > 0) {
     long long left = std::max(0, cap - P->p.refine_lam1_iters);
     for (int i = 0; i < sched->nlevels && left > 0; ++i) {
       const int n = (int)std::min<long long>(std::max(0, sched->iters[i]), left);
       if (n > 0 && sched->lam[i] > 1.0) {
-        clam.push_back(sched->lam[i]);
-        citers.push_back(n);
+        J.clam.push_back(sched->lam[i]);
+        J.citers.push_back(n);
         left -= n;
       }
     }
-    clam.push_back(1.0);
-    citers.push_back(0);
-    csched.lam = clam.data();
-    csched.iters = citers.data();
-    csched.nlevels = (int)clam.size();
+    J.clam.push_back(1.0);
+    J.citers.push_back(0);
+    J.csched.lam = J.clam.data();
+    J.csched.iters = J.citers.data();
+    J.csched.nlevels = (int)J.clam.size();
   }
-  // one correction: s_acc <- s_acc - WF(residual of s_acc)
-  auto correct = [&]() -> int {
-    // residual of the accumulated s: Delta d_u (data) and (S^-1 s)_m (source)
-    int rc2 = enqueue_resid_map(P, P->s_acc, P->rho, P->jmap);
-    if (rc2) return rc2;
-    CKI(launch_pack_data(P->dn, P->dn_orig, P->rho, npx / 2, P->part + 3 * P->nrow, P->st, P->stream));
+  *done = false;
+  return WF_OK;
+}
+
+// one correction, s_acc <- s_acc - WF(residual of s_acc): the problem of the
+// correction solve (its run follows with J.csched at J.tol * refine_tol_scale
+// and the plan's max_iters set to the correction cap) ...
+int wf::job_corr_begin(SolveJob& J) {
+  wf_plan_t P = J.P;
+  const size_t npx = (size_t)P->ny * P->nx;
+  const size_t nhb = (size_t)P->ny * P->M * sizeof(float2);
+  // residual of the accumulated s: Delta d_u (data) and (S^-1 s)_m (source)
+  int rc = enqueue_resid_map(P, P->s_acc, P->rho, P->jmap);
+  if (rc) return rc;
+  CKI(launch_pack_data(P->dn, P->dn_orig, P->rho, npx / 2, P->part + 3 * P->nrow, P->st, P->stream));
+  P->launches += 2;
+  if (J.with_src) {
+    // j^ = 2D DFT of the masked-pixel source, column-tiled
+    RowArgs ra = row_args(P);
+    ra.in_px = P->jmap;
+    ra.out_rf = P->r_q;
+    CKI(launch_row(ROW_R2C, ra, P->stream));
+    ColArgs ca = col_args(P, 0);
+    ca.in = P->r_q;
+    ca.out = P->src_2df;
+    CKI(launch_col(COL_FWD_TILED, ca, P->stream));
     P->launches += 2;
-    if (with_src) {
-      // j^ = 2D DFT of the masked-pixel source, column-tiled
-      RowArgs ra = row_args(P);
-      ra.in_px = P->jmap;
-      ra.out_rf = P->r_q;
-      CKI(launch_row(ROW_R2C, ra, P->stream));
-      ColArgs ca = col_args(P, 0);
-      ca.in = P->r_q;
-      ca.out = P->src_2df;
-      CKI(launch_col(COL_FWD_TILED, ca, P->stream));
-      P->launches += 2;
-      P->has_src = true;
-    }
-    CK(cudaMemsetAsync(P->f_x, 0, nhb, P->stream));
-    if (P->f_d1) CK(cudaMemsetAsync(P->f_d1, 0, nhb, P->stream));
-    if (P->f_t1) CK(cudaMemsetAsync(P->f_t1, 0, nhb, P->stream));
-    if (P->f_y) CK(cudaMemsetAsync(P->f_y, 0, nhb, P->stream));
-    if (P->f_t0) CK(cudaMemsetAsync(P->f_t0, 0, nhb, P->stream));
-    P->it_done = 0;
-    wf_stats sr{};
-    const int main_cap = P->p.max_iters;
-    if (P->p.refine_max_iters > 0) P->p.max_iters = P->p.refine_max_iters;
-    int sr_status = wf_run(P, &csched, tol * P->p.refine_tol_scale, &sr);
-    P->p.max_iters = main_cap;
-    if (finished(sr_status)) rc2 = wf_get_field(P, WF_FIELD_S, P->s_corr);
-    P->has_src = false;
-    if (!finished(sr_status)) return sr_status;
-    if (rc2) return rc2;
-    // a correction that runs to refine_max_iters has done what was asked
-    if (sr_status != WF_OK && P->p.refine_max_iters == 0 && status == WF_OK) status = sr_status;
-    tot.iters += sr.iters;
-    tot.checkpoints += sr.checkpoints;
-    CKI(launch_sub(P->s_acc, P->s_corr, npx, P->stream));
-    P->launches += 1;
-    return WF_OK;
-  };
-  // residual of the refined s against the original problem, into h_st
-  auto residual_of_refined = [&]() -> int {
-    int rc2 = enqueue_resid_map(P, P->s_acc, P->rho, nullptr);
-    if (rc2) return rc2;
-    CK(cudaMemcpyAsync(&P->st->du2, &du2, sizeof(double), cudaMemcpyHostToDevice, P->stream));
-    CtrlArgs c = ctrl_args(P);
-    c.count_iters = 0;
-    CKI(launch_ctrl(c, P->stream));
-    P->launches += 1;
-    CK(cudaMemcpyAsync(P->h_st, P->st, sizeof(WfState), cudaMemcpyDeviceToHost, P->stream));
-    CK(cudaStreamSynchronize(P->stream));
-    return WF_OK;
-  };
-  auto passes = [&]() { return P->h_st->rel_u <= tol * P->p.tol_u_scale && P->h_st->rel_m <= tol; };
-  for (int r = 0; r < P->p.refine; ++r)
-    if ((rc = correct())) return rc;
-  if ((rc = residual_of_refined())) return rc;
-  // further corrections only while the refined s fails the stop test
-  for (int r = 0; tol > 0 && r < P->p.refine_extra && !passes(); ++r) {
-    if ((rc = correct())) return rc;
-    if ((rc = residual_of_refined())) return rc;
+    P->has_src = true;
   }
-  const int where_ = ptr_where(s_out);
+  CK(cudaMemsetAsync(P->f_x, 0, nhb, P->stream));
+  if (P->f_d1) CK(cudaMemsetAsync(P->f_d1, 0, nhb, P->stream));
+  if (P->f_t1) CK(cudaMemsetAsync(P->f_t1, 0, nhb, P->stream));
+  if (P->f_y) CK(cudaMemsetAsync(P->f_y, 0, nhb, P->stream));
+  if (P->f_t0) CK(cudaMemsetAsync(P->f_t0, 0, nhb, P->stream));
+  P->it_done = 0;
+  J.main_cap = P->p.max_iters;
+  if (P->p.refine_max_iters > 0) P->p.max_iters = P->p.refine_max_iters;
+  return WF_OK;
+}
+
+// ... and, after that run, the subtraction
+int wf::job_corr_end(SolveJob& J, int run_status, const wf_stats& sr) {
+  wf_plan_t P = J.P;
+  const size_t npx = (size_t)P->ny * P->nx;
+  P->p.max_iters = J.main_cap;
+  int rc = WF_OK;
+  if (finished_rc(run_status)) rc = wf_get_field(P, WF_FIELD_S, P->s_corr);
+  P->has_src = false;
+  if (!finished_rc(run_status)) return run_status;
+  if (rc) return rc;
+  // a correction that runs to refine_max_iters has done what was asked
+  if (run_status != WF_OK && P->p.refine_max_iters == 0 && J.status == WF_OK) J.status = run_status;
+  J.tot.iters += sr.iters;
+  J.tot.checkpoints += sr.checkpoints;
+  CKI(launch_sub(P->s_acc, P->s_corr, npx, P->stream));
+  P->launches += 1;
+  J.corrections += 1;
+  return WF_OK;
+}
+
+// residual of the refined s against the original problem, into h_st
+int wf::job_refined_residual(SolveJob& J) {
+  wf_plan_t P = J.P;
+  int rc = enqueue_resid_map(P, P->s_acc, P->rho, nullptr);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(&P->st->du2, &J.du2, sizeof(double), cudaMemcpyHostToDevice, P->stream));
+  CtrlArgs c = ctrl_args(P);
+  c.count_iters = 0;
+  CKI(launch_ctrl(c, P->stream));
+  P->launches += 1;
+  CK(cudaMemcpyAsync(P->h_st, P->st, sizeof(WfState), cudaMemcpyDeviceToHost, P->stream));
+  CK(cudaStreamSynchronize(P->stream));
+  return WF_OK;
+}
+
+bool wf::job_passes(const SolveJob& J) {
+  const wf_plan_t P = J.P;
+  return P->h_st->rel_u <= J.tol * P->p.tol_u_scale && P->h_st->rel_m <= J.tol;
+}
+
+int wf::job_finish(SolveJob& J) {
+  wf_plan_t P = J.P;
+  const size_t npx = (size_t)P->ny * P->nx;
+  const int where_ = ptr_where(J.s_out);
   if (where_ == PTR_OTHER_DEVICE) return WF_EINVAL;
   const bool dev = where_ == PTR_DEVICE;
-  CK(cudaMemcpyAsync(s_out, P->s_acc, npx * sizeof(float), dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+  CK(cudaMemcpyAsync(J.s_out, P->s_acc, npx * sizeof(float), dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                      P->stream));
   CK(cudaStreamSynchronize(P->stream));
   // the plan now holds the last correction problem, not the caller's
   P->loaded = false;
-  tot.rel_rho_u = P->h_st->rel_u;
-  tot.rel_rho_m = P->h_st->rel_m;
-  if (tol > 0) {
+  J.tot.rel_rho_u = P->h_st->rel_u;
+  J.tot.rel_rho_m = P->h_st->rel_m;
+  if (J.tol > 0) {
     // the refined s is judged by the stop test itself
-    status = passes() ? WF_OK : (status == WF_OK ? WF_ENOCONV : status);
+    J.status = job_passes(J) ? WF_OK : (J.status == WF_OK ? WF_ENOCONV : J.status);
   }
-  tot.status = status;
-  if (st) *st = tot;
-  return status;
+  J.tot.status = J.status;
+  if (J.st) *J.st = J.tot;
+  return WF_OK;
+}
+
+int wf::plan_refine(const wf_plan_t P) { return P->p.refine; }
+int wf::plan_refine_extra(const wf_plan_t P) { return P->p.refine_extra; }
+double wf::plan_refine_tol_scale(const wf_plan_t P) { return P->p.refine_tol_scale; }
+
+static int solve_impl(wf_plan_t P, const float* d, const float* pixel_var, const uint8_t* mask, const float* C,
+                      const float* P1f, const float* Pst, const float* stripe_amp2, const float* s_init,
+                      const wf_schedule* sched, double tol, float* s_out, wf_stats* st) {
+  SolveJob J;
+  J.P = P;
+  J.sched = sched;
+  J.tol = tol;
+  J.s_out = s_out;
+  J.st = st;
+  int rc = job_start(J, d, pixel_var, mask, C, P1f, Pst, stripe_amp2, s_init);
+  if (rc) return rc;
+  wf_stats s0{};
+  bool done = false;
+  rc = job_after_first(J, wf_run(P, sched, tol, &s0), s0, &done);
+  if (rc || done) return rc ? rc : J.status;
+  auto correction = [&]() -> int {
+    int r = job_corr_begin(J);
+    if (r) return r;
+    wf_stats sr{};
+    const int rs = wf_run(P, &J.csched, tol * P->p.refine_tol_scale, &sr);
+    return job_corr_end(J, rs, sr);
+  };
+  for (int r = 0; r < P->p.refine; ++r)
+    if ((rc = correction())) return rc;
+  if ((rc = job_refined_residual(J))) return rc;
+  // further corrections only while the refined s fails the stop test
+  for (int r = 0; tol > 0 && r < P->p.refine_extra && !job_passes(J); ++r) {
+    if ((rc = correction())) return rc;
+    if ((rc = job_refined_residual(J))) return rc;
+  }
+  if ((rc = job_finish(J))) return rc;
+  return J.status;
 }
 
 extern "C" {

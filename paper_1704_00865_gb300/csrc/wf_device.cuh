@@ -612,4 +612,53 @@ enum : unsigned {
 // (A^-1 + B^-1)^-1 (A^-1 a + B^-1 b) of eqs. (ew_t), (2mess_t1)-(2mess_t0).
 __device__ __forceinline__ float link_w(float A, float B) { return __fdividef(B, A + B); }
 
+// ---------------------------------------------------------------- grid barrier
+// (for cooperative launches whose CTAs are all resident: the one-launch sweep
+// of wf_fused.cu and the persistent batch of wf_batchk.cu)
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned ld_relaxed_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Waits this many polls at most (each a global load, about half a
+// microsecond); a sweep's barrier normally waits one or two microseconds.
+constexpr int WF_GRID_TRIES = 1 << 21;
+
+// All CTAs of the grid meet here.  bar[0] counts the arrivals of this launch
+// (zeroed before it starts); the k-th barrier of the launch is passed once
+// it reaches k * nblocks.  Each arrival is an acquire-release add (the CTA's
+// writes, ordered before it by the block barrier, are released; the last
+// arrival need not wait for a second word to change), and the waits are
+// acquire loads of the same word, so one round trip to L2 separates the
+// last arrival from the others' release.  bar[2] is the abort word.
+// Returns false, for every thread of the CTA, if the wait gave up or
+// another CTA aborted.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned target, int* ok_s, unsigned* err) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    unsigned seen;
+    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(seen) : "l"(bar) : "memory");
+    for (int i = 0; seen + 1u < target; ++i) {
+      if (i >= WF_GRID_TRIES || ld_relaxed_gpu(&bar[2]) != 0u) {
+        atomicExch(&bar[2], 1u);
+        atomicOr(err, WF_ERR_TIMEOUT);
+        ok = 0;
+        break;
+      }
+      seen = ld_acquire_gpu(bar) - 1u;
+    }
+    *ok_s = ok;
+  }
+  __syncthreads();
+  return *ok_s != 0;
+}
+
+
 }  // namespace wf

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/wf.h"
 
 namespace wf {
@@ -174,6 +176,95 @@ struct FusedArgs {
 int launch_fused(const FusedArgs& a, cudaStream_t s);
 // whether the one-launch sweep handles this plan on the current device
 bool fused_supported(int ny, int nx, int has_rf, int merged, int prec);
+
+// One map of a persistent batch (wf_batchk.cu): its size class and the
+// fields and tables its row and column items use.
+struct BatchMapArgs {
+  int cls;                    // 2 * (index of the size) + shape, batch_class()
+  const float4* dn;
+  float2* f_d1;
+  float2* f_t1;
+  float2* f_x;
+  const float2* eig;
+  const float2* eig_nyq;
+  const float* pst;
+  const float* a2;            // or nullptr
+  const float2* twx;
+  const float2* twh;
+  const float2* twy;
+  const float2* src;          // 2D-Fourier source (defect correction) or nullptr
+  WfState* st;
+};
+struct BatchArgs {
+  const BatchMapArgs* maps;
+  const int2* row_items;      // (map, row group) work queue of the row phase
+  const int2* col_items;      // (map, column group) work queue of the column phase
+  int n_row, n_col;
+  int nsweeps;
+  unsigned* bar;              // grid barrier words (zeroed before each launch)
+  unsigned* queue;            // 2 nsweeps work counters (zeroed before each launch)
+  unsigned* err;              // WF_ERR_TIMEOUT if a barrier wait gave up
+};
+int batch_class(int n, int variant);            // -1: size not handled
+bool batch_has_second_shape(int n);
+int batch_item_shape(int cls, int* rows_per_item, int* cols_per_item, int* row_values, int* col_values);
+int batch_grid();                                 // CTAs of a launch (0: cannot launch)
+int launch_batch_sweeps(const BatchArgs& a, int grid, cudaStream_t s);
+
+// Device buffers of a persistent batch and the runner that iterates several
+// loaded plans together (wf_api.cu).
+struct BatchDevice {
+  BatchMapArgs* maps = nullptr;
+  int2* rows = nullptr;
+  int2* cols = nullptr;
+  unsigned* bar = nullptr;    // 4 words
+  unsigned* queue = nullptr;  // 2 residual_every words
+  unsigned* err = nullptr;
+  size_t cap_maps = 0, cap_items = 0;
+  int grid = 0;               // CTAs of a launch
+  long long launches = 0;     // persistent launches so far
+  long long per_plan_launches = 0;
+  std::vector<int2> row_items, col_items;
+};
+int plan_batch_map(wf_plan_t P, int variant, BatchMapArgs* out);
+bool plan_batch_ok(const wf_plan_t P);
+int plan_size(const wf_plan_t P);
+int plan_autotune(const wf_plan_t P);
+int time_batch_variant(wf_plan_t P, int variant, BatchDevice& bd, cudaStream_t s, double* us);
+int run_plans_persistent(const std::vector<wf_plan_t>& plans, const std::vector<int>& variant,
+                         const wf_schedule* sch, double tol, BatchDevice& bd, cudaStream_t s,
+                         std::vector<int>& status, std::vector<wf_stats>& st);
+
+// The steps of one wf_solve (wf_api.cu): load, first run, corrections,
+// refined residual, output.  A persistent batch takes each step for all its
+// maps and runs their iterations together between the steps.
+struct SolveJob {
+  wf_plan_t P = nullptr;
+  const wf_schedule* sched = nullptr;
+  double tol = 0.0;
+  float* s_out = nullptr;
+  wf_stats* st = nullptr;
+  int status = WF_OK;
+  wf_stats tot{};
+  double du2 = 0.0;
+  bool with_src = false;
+  wf_schedule csched{};        // schedule of the correction solves
+  std::vector<double> clam;
+  std::vector<int> citers;
+  int main_cap = 0;            // max_iters while a correction's cap is in force
+  int corrections = 0;
+};
+int job_start(SolveJob& J, const float* d, const float* pixel_var, const uint8_t* mask, const float* C,
+              const float* P1f, const float* Pst, const float* stripe_amp2, const float* s_init);
+int job_after_first(SolveJob& J, int run_status, const wf_stats& s0, bool* done);
+int job_corr_begin(SolveJob& J);
+int job_corr_end(SolveJob& J, int run_status, const wf_stats& sr);
+int job_refined_residual(SolveJob& J);
+bool job_passes(const SolveJob& J);
+int job_finish(SolveJob& J);
+int plan_refine(const wf_plan_t P);
+int plan_refine_extra(const wf_plan_t P);
+double plan_refine_tol_scale(const wf_plan_t P);
 
 // setup / control kernels
 struct SetupArgs {

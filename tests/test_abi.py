@@ -137,10 +137,13 @@ def test_schedule_struct_layout_matches_header(lib, tmp_path):
 
 @pytest.mark.parametrize("sizes,lanes,parts,code", [
     ([], 4, 7, 1),                           # no maps
-    ([(64, 64)], 0, 7, 1),                   # no lanes
     ([(64, 64)], 65, 7, 1),                  # too many lanes
     ([(64, 64), (64, 1000)], 2, 7, 7),       # one unsupported size
     ([(64, 64), (128, 32)], 2, 6, 1),        # white part missing
+    ([(64, 64)], 0, 7, 7),                   # persistent mode: size its kernel does not take
+    ([(256, 256), (256, 512)], 0, 7, 7),     # persistent mode: not square
+    ([(256, 256)], 0, 3, 7),                 # persistent mode: no stripe part
+    ([(256, 256)], -1, 7, 1),                # negative lanes
 ])
 def test_batch_create_rejects_bad_arguments_before_any_cuda_call(lib, sizes, lanes, parts, code):
     from paper_1704_00865_gb300 import wf

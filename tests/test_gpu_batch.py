@@ -85,3 +85,86 @@ def test_batch_reports_the_first_error(wf):
         b.solve([_arrays(probs[0], True), tuple(bad)], wf.make_schedule("fixed", [10.0], [10]), 1e-5, outs)
     assert e.value.code == wf.WF_ENOTPD
     b.close()
+
+
+# ---------------------------------------------------------------- persistent mode (lanes = 0)
+
+def _batch_solve(wf, probs, lanes, sched, tol, **params):
+    import torch
+    shapes = [p.shape for p in probs]
+    b = wf.Batch(shapes, params=wf.make_params(**params), lanes=lanes)
+    inputs = [tuple(dev(a) for a in (p.d, p.pixel_var, p.mask, p.C, p.P1f, p.Pst, p.stripe_amp2)) for p in probs]
+    outs = [torch.empty(*sh, device="cuda") for sh in shapes]
+    rc, stats = b.solve(inputs, sched, tol, outs)
+    b.close()
+    return rc, stats, [o.cpu().numpy().astype(np.float64) for o in outs]
+
+
+@pytest.mark.parametrize("shape_choice", [0, 2])
+def test_persistent_batch_matches_the_oracle_sweep_for_sweep(wf, shape_choice):
+    # every size the persistent kernel takes, one map each (two of 256), a
+    # fixed schedule run to its cap: each map's s against the FP64 oracle's
+    # messenger iteration with the same schedule, for both compiled shapes
+    import os
+    O.set_workers(os.cpu_count() or 1)
+    sizes = [256, 384, 256, 512, 768, 1024, 1536, 2048]
+    probs = [synth.make_problem(n, n, 4100 + i, amp_jitter=0.5, stripe_rows_vary=(i % 2 == 1))
+             for i, n in enumerate(sizes)]
+    lam, its = [30.0, 3.0, 1.0], [20, 20, 20]
+    sched = wf.make_schedule("fixed", lam, its)
+    rc, stats, outs = _batch_solve(wf, probs, 0, sched, 0.0, residual_every=10, max_iters=60,
+                                   autotune=shape_choice)
+    assert rc == wf.WF_ENOCONV  # tol = 0: every map runs to max_iters
+    for p, st, s in zip(probs, stats, outs):
+        assert st["iters"] == 60 and st["lam_final"] == 1.0, st
+        r = O.messenger_solve(p, schedule=O.fixed_schedule(lam, its), n_iters=60, residual_every=10,
+                              merge_2df=True, split_f=0.5, split_fp=0.5)
+        err = rel(s, r["s"])
+        assert err < 1e-4, (p.shape, err)
+        # the residual each map's stop test reads
+        assert abs(st["rel_rho_u"] - r["rel_u"]) < 2e-3 * r["rel_u"], (p.shape, st, r["rel_u"])
+
+
+def test_persistent_batch_refined_solves_agree_with_single_map_solves(wf):
+    # the whole solve (first run, corrections with their masked-pixel source,
+    # the refined s) for each map of a mixed batch, against the same solve of
+    # each map alone (lanes = 1, the per-map kernels)
+    sizes = [512, 256, 1024, 384, 256]
+    probs = [synth.make_problem(n, n, 4200 + i, amp_jitter=0.5) for i, n in enumerate(sizes)]
+    sched = wf.make_schedule("fixed", [30.0, 3.0], [200, 200])
+    kw = dict(residual_every=20, max_iters=400, refine=2, refine_max_iters=300, refine_lam1_iters=100,
+              refine_tol_scale=1.0, autotune=0)
+    rc, stats, outs = _batch_solve(wf, probs, 0, sched, 0.0, **kw)
+    _, stats1, outs1 = _batch_solve(wf, probs, 1, sched, 0.0, **kw)
+    for p, a, b, sa, sb in zip(probs, outs, outs1, stats, stats1):
+        assert sa["iters"] == sb["iters"] == 1000, (p.shape, sa, sb)
+        assert rel(a, b) < 1e-5, (p.shape, rel(a, b))
+
+
+def test_persistent_batch_maps_stop_on_their_own_test(wf):
+    # per-map done flags: each map leaves the shared launches at the first
+    # checkpoint where its own stop test passes, as it does alone
+    sizes = [256, 512, 256, 384]
+    probs = [synth.make_problem(n, n, 4300 + i, amp_jitter=0.5, k_knee=4.0, k_knee_x=4.0)
+             for i, n in enumerate(sizes)]
+    sched = wf.make_schedule("fixed", O.cooling_levels(1e2, 5), [40] * 5)
+    kw = dict(residual_every=10, max_iters=20000, tol_u_scale=50.0, autotune=0)
+    rc, stats, outs = _batch_solve(wf, probs, 0, sched, 3e-5, **kw)
+    _, stats1, outs1 = _batch_solve(wf, probs, 1, sched, 3e-5, **kw)
+    assert rc == wf.WF_OK, stats
+    for p, a, b, sa, sb in zip(probs, outs, outs1, stats, stats1):
+        assert sa["status"] == 0 and abs(sa["iters"] - sb["iters"]) <= 10, (p.shape, sa, sb)
+        assert rel(a, b) < 1e-4, (p.shape, rel(a, b))
+    assert len({s["iters"] for s in stats}) > 1, stats
+
+
+def test_persistent_batch_rejects_what_its_kernel_does_not_take(wf):
+    with pytest.raises(wf.WFError) as e:
+        wf.Batch([(256, 256), (256, 512)], lanes=0)
+    assert e.value.code == wf.WF_EUNSUPPORTED
+    with pytest.raises(wf.WFError) as e:
+        wf.Batch([(128, 128)], lanes=0)
+    assert e.value.code == wf.WF_EUNSUPPORTED
+    with pytest.raises(wf.WFError) as e:
+        wf.Batch([(256, 256)], params=wf.make_params(merge_2df=0, split_fp=0.3), lanes=0)
+    assert e.value.code == wf.WF_EUNSUPPORTED
