@@ -724,7 +724,10 @@ def run_passes(args):
     return 0
 
 
-PRECISIONS = {0: "fp32", 1: "tf32 split (3 products)", 2: "tf32 (1 product)"}
+PRECISIONS = {0: "fp32", 1: "tf32 split (3 products), mma.sync", 2: "tf32 (1 product), mma.sync",
+              3: "tf32 split (3 products), tcgen05", 4: "tf32 (1 product), tcgen05"}
+# column lengths the tcgen05 stages take (their operand tiles need shared memory)
+TC5_SIZES = (512, 1024)
 PRECISION_SIZES = (1024, 4096)
 
 
@@ -764,6 +767,8 @@ def run_precision(args):
         entry = {"solves_per_s": round(1e3 * len(ms) / sum(ms), 4), "status": st["status"],
                  "sweeps": st["iters"], "final_rel_rho_u": st["rel_rho_u"], "final_rel_rho_m": st["rel_rho_m"]}
         for n in PRECISION_SIZES:
+            if prec >= 3 and n not in TC5_SIZES:
+                continue
             p = synth.make_problem(n, n, SEED + n)
             pl = wf.Plan(n, n, wf.parts_of(p), wf.make_params(merge_2df=1, split_f=SPLIT_F, split_fp=SPLIT_FP,
                                                                dft_precision=prec))
@@ -792,9 +797,9 @@ def main():
     ap.add_argument("--size", type=int, default=N, help="map side for --workload passes")
     ap.add_argument("--autotune", type=int, default=1, choices=[0, 1, 2],
                     help="pass shapes for --workload passes: 1 timed (default), 0 first, 2 second shapes")
-    ap.add_argument("--dft-precision", type=int, default=0, choices=[0, 1, 2],
+    ap.add_argument("--dft-precision", type=int, default=0, choices=[0, 1, 2, 3, 4],
                     help="radix-16 stages of the column transforms for --workload passes: 0 FP32, "
-                         "1 split TF32 tensor cores, 2 TF32 tensor cores")
+                         "1 split TF32 (mma.sync), 2 TF32 (mma.sync), 3 split TF32 (tcgen05), 4 TF32 (tcgen05)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -212,10 +212,11 @@ int wf::check_plan_args(int ny, int nx, unsigned parts, const wf_params* p) {
   if (prm.refine < 0 || prm.refine > 8 || !(prm.refine_tol_scale >= 1.0) || prm.refine_max_iters < 0 ||
       prm.refine_lam1_iters < 0 || prm.stall_checks < 0 || prm.autotune < 0 || prm.autotune > 2 ||
       prm.refine_extra < 0 || prm.refine_extra > 8 ||
-      prm.dft_precision < 0 || prm.dft_precision > 2 || prm.sweep_kernel < 0 || prm.sweep_kernel > 1)
+      prm.dft_precision < 0 || prm.dft_precision > 4 || prm.sweep_kernel < 0 || prm.sweep_kernel > 1)
     return WF_EINVAL;
   // tensor-core radix-16 stages: 16-value column shapes, merged 2DF block
   if (prm.dft_precision != 0 && (!col_tc_supported(ny) || prm.merge_2df != 1)) return WF_EUNSUPPORTED;
+  if (prm.dft_precision >= 3 && !col_tc5_supported(ny)) return WF_EUNSUPPORTED;
   return WF_OK;
 }
 

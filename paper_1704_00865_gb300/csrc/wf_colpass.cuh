@@ -98,6 +98,19 @@ __device__ __forceinline__ void tile_load_rowmajor(float2* dst, const float2* sr
   }
 }
 
+// Extra shared memory of the tcgen05 stages (PREC 3, 4) after the column
+// pass's own: 1 KB of alignment slack, the A tiles (16 KB per 128 threads,
+// twice for the split), the four 4 KB DFT matrices, the mbarrier.
+template <int L, int MODE, int EV, int PREC>
+struct Tc5Smem {
+  static constexpr int tiles = ColPassCfg<L, MODE, EV>::THREADS / 128;
+  static constexpr size_t bytes = PREC >= 3 ? 1024 + (size_t)tiles * 16384 * (PREC == 3 ? 2 : 1) + 16384 + 16 : 0;
+};
+template <int L, int MODE, int EV, int PREC>
+__device__ __forceinline__ uint64_t* tc5_mbar(unsigned char* smem) {
+  return reinterpret_cast<uint64_t*>(smem + ColPassCfg<L, MODE, EV>::bytes + Tc5Smem<L, MODE, EV, PREC>::bytes - 16);
+}
+
 // The column pass (Sec. 2 / Appendix A: the 2D-Fourier updates between the
 // forward and inverse column DFTs).  The messenger tile and the (C, P1f)
 // tile are staged in shared memory before the transform begins.
@@ -177,6 +190,10 @@ col_pass_kernel(ColArgs a) {
     drain();
     return;
   }
+  // radix-16 stages on tcgen05: operand tiles, DFT matrices, TMEM (after the
+  // early returns, so every path that allocates also releases)
+  if constexpr (PREC >= 3)
+    tc5_setup<L, PREC>(smem + Cfg::bytes, tc5_mbar<L, MODE, EV, PREC>(smem), Cfg::TWS ? s_tw : a.twy, 1);
 
   float2 v[E];
 #pragma unroll
@@ -240,6 +257,10 @@ col_pass_kernel(ColArgs a) {
     if (blockIdx.x == 0 && threadIdx.x == 0) a.st->T0s[a.parity ^ 1] = T0;
   }
   fft_block<L, E, true, false, Cfg::TWS, PREC>(v, sb, t, Cfg::TWS ? s_tw : a.twy, 1);
+  if constexpr (PREC >= 3) {
+    tc5_teardown();
+    if (threadIdx.x == 0 && !tc5_ctx().ok) atomicOr(&a.st->err, WF_ERR_TIMEOUT);
+  }
   if constexpr (!WF_PDL_EARLY) pdl_trigger();
   const float sc = 1.0f / (float)L;
 #pragma unroll
@@ -251,7 +272,9 @@ static int launch_col_pass_e(const ColArgs& a, cudaStream_t s) {
   using Cfg = ColPassCfg<L, MODE, EV>;
   const int ncols = a.nx / 2;
   if (ncols % Cfg::W != 0) return (int)cudaErrorInvalidValue;
-  constexpr size_t kBytes = Cfg::bytes;
+  constexpr size_t kBytes = Cfg::bytes + Tc5Smem<L, MODE, EV, PREC>::bytes;
+  static_assert(kBytes <= kMaxSmem, "column pass staging exceeds shared memory");
+  static_assert(PREC < 3 || Cfg::THREADS % 128 == 0, "tcgen05 tiles are 128 threads");
   // once per instantiation and process (plans may run on several host threads)
   static std::once_flag once;
   static cudaError_t cfg_err = cudaSuccess;

@@ -87,19 +87,35 @@ int col_dft_p(int inverse, const ColArgs& a, cudaStream_t s) {
   }
 }
 
+// tcgen05 stages (PREC 3, 4): the column pass for 512- and 1024-long
+// columns, where the operand tiles fit beside the pass's own staging
+template <int PREC>
+int col_pass_tc5_p(int L, int mode, const ColArgs& a, cudaStream_t s) {
+  switch (L) {
+    case 512: return col_pass_tc_L<512, PREC>(mode, a, s);
+    case 1024: return col_pass_tc_L<1024, PREC>(mode, a, s);
+    default: return (int)cudaErrorInvalidValue;
+  }
+}
+
 }  // namespace
 
 bool col_tc_supported(int L) { return L == 512 || L == 1024 || L == 2048 || L == 4096; }
+bool col_tc5_supported(int L) { return L == 512 || L == 1024; }
 
 int launch_col_pass_tc(int L, int mode, const ColArgs& a, cudaStream_t s) {
   if (a.prec == 1) return col_pass_tc_p<1>(L, mode, a, s);
   if (a.prec == 2) return col_pass_tc_p<2>(L, mode, a, s);
+  if (a.prec == 3) return col_pass_tc5_p<3>(L, mode, a, s);
+  if (a.prec == 4) return col_pass_tc5_p<4>(L, mode, a, s);
   return (int)cudaErrorInvalidValue;
 }
 
+// wf_fft2's column DFTs: the tcgen05 precisions take the mma.sync stages of
+// the same arithmetic (3 -> split TF32, 4 -> TF32)
 int launch_col_dft_tc(int inverse, const ColArgs& a, cudaStream_t s) {
-  if (a.prec == 1) return col_dft_p<1>(inverse, a, s);
-  if (a.prec == 2) return col_dft_p<2>(inverse, a, s);
+  if (a.prec == 1 || a.prec == 3) return col_dft_p<1>(inverse, a, s);
+  if (a.prec == 2 || a.prec == 4) return col_dft_p<2>(inverse, a, s);
   return (int)cudaErrorInvalidValue;
 }
 

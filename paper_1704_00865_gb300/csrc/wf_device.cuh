@@ -327,6 +327,290 @@ __device__ __forceinline__ void tc_radix16_stage(float2 (&v)[16], float2* sb, in
   }
 }
 
+// ---------------------------------------------------------------- TMA bulk copies
+// 1D bulk copies global -> shared (cp.async.bulk) completed on an mbarrier.
+// Addresses and sizes must be multiples of 16 bytes.
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// make barrier initialisation visible to the async (TMA) proxy
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// Bounded wait for phase `phase` of the barrier; false if it gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, int max_tries) {
+  for (int i = 0; i < max_tries; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+// try_wait already suspends for a hardware-chosen interval per attempt; this
+// many attempts is far beyond the microseconds a bulk copy takes.
+constexpr int WF_WAIT_TRIES = 1 << 20;
+
+// Ampere-style asynchronous copies (16 or 8 bytes per thread) for strided tiles.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// ---------------------------------------------------------------- tcgen05 radix-16
+// The same radix-16 stage on the 5th-generation tensor cores: each 128-thread
+// group of the block is one tcgen05.mma tile whose M = 128 rows are the
+// group's transforms (one per thread), with the complex product written as
+// one real product of K = N = 32:
+//   [Yr | Yi] (128 x 32) = [Ur | Ui] (128 x 32) . G,   G^T (32 x 32) =
+//   [[Fr, -Fi], [Fi, Fr]]  (rows: outputs Yr[k], then Yi[k]; columns: Ur[r], Ui[r]),
+// TF32 operands in shared memory, FP32 accumulators in tensor memory (TMEM
+// lane = row = transform, column = output), read back with tcgen05.ld by
+// the thread that owns the transform.  PREC = 3 splits both factors into
+// two TF32 parts (lo*hi + hi*lo + hi*hi, small terms first), PREC = 4 takes
+// hi*hi alone.  One thread issues the 4 (K = 8 each; 12 for the split) MMAs
+// of every tile and commits them to an mbarrier that all threads wait on.
+//
+// Operand layout (both A and B = G^T, 32 K-values per row, K-major, no
+// swizzle): core matrices of 8 rows x 16 bytes, 128 bytes apart along K
+// (leading byte offset) and 1024 bytes apart between 8-row groups (stride
+// byte offset).
+
+// block state of the tcgen05 stages, set up by the kernel that uses them
+struct Tc5Ctx {
+  uint32_t a_hi, a_lo;                              // A tiles, 16 KB per 128 threads
+  uint32_t b_fwd_hi, b_fwd_lo, b_inv_hi, b_inv_lo;  // G^T, 4 KB each
+  uint32_t mbar;                                    // MMA completion barrier
+  uint32_t tmem;                                    // TMEM base (lane 0, column 0)
+  uint32_t phase;                                   // parity of the next completion
+  uint32_t ntiles;
+  uint32_t ok;                                      // 0 once a bounded wait gave up
+};
+__device__ __forceinline__ Tc5Ctx& tc5_ctx() {
+  __shared__ Tc5Ctx c;
+  return c;
+}
+// byte offset of element (row, k) in a K-major no-swizzle 32-column operand
+__device__ __forceinline__ uint32_t tc5_off(int row, int k) {
+  return (uint32_t)((row >> 3) * 1024 + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4);
+}
+// shared-memory matrix descriptor: start address, leading byte offset 128,
+// stride byte offset 1024, the fixed 0b001 at bits 46-48, no swizzle
+__device__ __forceinline__ uint64_t tc5_desc(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)(128u >> 4) << 16) | ((uint64_t)(1024u >> 4) << 32) |
+         (1ull << 46);
+}
+// instruction descriptor of kind::tf32: F32 accumulator (bits 4-5 = 1), TF32
+// A and B (bits 7-9, 10-12 = 2), both K-major, N = 32 (bits 17-22 = N >> 3),
+// M = 128 (bits 24-28 = M >> 4)
+constexpr uint32_t kTc5Idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void tc5_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(kTc5Idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void tc5_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+__device__ __forceinline__ void tc5_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc5_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// whole warp: allocate ncols TMEM columns (power of two, >= 32), address to *dst
+__device__ __forceinline__ void tc5_alloc(uint32_t dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tc5_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+// 32 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tc5_ld32(uint32_t taddr, float (&y)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) y[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void sts_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  asm volatile("st.shared.v4.b32 [%0], {%1,%2,%3,%4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
+}
+// bounded wait for phase `phase` of an mbarrier given by its shared address
+__device__ __forceinline__ bool mbar_wait_addr(uint32_t bar, uint32_t phase, int max_tries) {
+  for (int i = 0; i < max_tries; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(bar), "r"(phase)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+template <int L, int NS, bool INV, bool TWS, int PREC>
+__device__ __forceinline__ void tc5_radix16_stage(float2 (&v)[16], float2* sb, int t,
+                                                  const float2* __restrict__ twtab, int twstride) {
+  Tc5Ctx& cx = tc5_ctx();
+  if constexpr (NS > 1) {
+    const int jm = t % NS;
+    const int step = jm * (L / (NS * 16)) * twstride;
+    float2 w1 = tw_dir<INV>(tw_load<TWS>(twtab, step));
+    float2 wr = w1;
+#pragma unroll
+    for (int r = 1; r < 16; ++r) {
+      if ((r & 3) == 0) wr = tw_dir<INV>(tw_load<TWS>(twtab, step * r));
+      v[r] = cmul(v[r], wr);
+      wr = cmul(wr, w1);
+    }
+  }
+  // this thread's transform is row `row` of its group's A tile
+  const int tile = threadIdx.x >> 7, row = threadIdx.x & 127;
+  const uint32_t ahi = cx.a_hi + (uint32_t)tile * 16384u, alo = cx.a_lo + (uint32_t)tile * 16384u;
+#pragma unroll
+  for (int kc = 0; kc < 8; ++kc) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int k = 4 * kc + q;
+      const float x = k < 16 ? v[k].x : v[k - 16].y;
+      tf32_split<PREC == 3 ? 1 : 2>(x, h[q], l[q]);
+    }
+    sts_v4(ahi + tc5_off(row, 4 * kc), h[0], h[1], h[2], h[3]);
+    if constexpr (PREC == 3) sts_v4(alo + tc5_off(row, 4 * kc), l[0], l[1], l[2], l[3]);
+  }
+  const uint32_t ph = cx.phase;
+  fence_async_smem();  // the generic-proxy stores above, seen by the tensor cores
+  tc5_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    tc5_fence_after();
+    const uint32_t bhi = INV ? cx.b_inv_hi : cx.b_fwd_hi, blo = INV ? cx.b_inv_lo : cx.b_fwd_lo;
+    for (uint32_t tl = 0; tl < cx.ntiles; ++tl) {
+      const uint32_t d = cx.tmem + 32u * tl;
+      const uint32_t ah = cx.a_hi + tl * 16384u, al = cx.a_lo + tl * 16384u;
+      uint32_t acc = 0;
+      if constexpr (PREC == 3) {
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          tc5_mma(d, tc5_desc(al + 256u * s), tc5_desc(bhi + 256u * s), acc);
+          acc = 1;
+        }
+#pragma unroll
+        for (int s = 0; s < 4; ++s) tc5_mma(d, tc5_desc(ah + 256u * s), tc5_desc(blo + 256u * s), 1);
+      }
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        tc5_mma(d, tc5_desc(ah + 256u * s), tc5_desc(bhi + 256u * s), acc);
+        acc = 1;
+      }
+    }
+    tc5_commit(cx.mbar);
+  }
+  if (!mbar_wait_addr(cx.mbar, ph, WF_WAIT_TRIES)) cx.ok = 0u;
+  tc5_fence_after();
+  float y[32];
+  tc5_ld32(cx.tmem + ((uint32_t)(32 * ((threadIdx.x >> 5) & 3)) << 16) + 32u * (uint32_t)tile, y);
+  tc5_fence_before();
+  __syncthreads();  // every thread has passed the wait and read its outputs
+  if (threadIdx.x == 0) cx.phase = ph ^ 1u;
+  // outputs to their autosort positions, as the FP32 stage stores them
+  const int jm = t % NS;
+  const int base = (t - jm) * 16 + jm;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) sb[spad(base + k * NS)] = make_float2(y[k], y[16 + k]);
+}
+
+// Block set-up of the tcgen05 stages (every thread calls it): the four G^T
+// matrices from the exact twiddle table, the mbarrier, the TMEM columns
+// (32 per 128-thread tile, warp 0 allocates), the context.  smem_ab starts a
+// region of 1 KB (alignment slack) + (PREC == 3 ? 2 : 1) * 16 KB per tile +
+// 16 KB.
+template <int L, int PREC>
+__device__ __forceinline__ void tc5_setup(unsigned char* smem_ab, uint64_t* mbar, const float2* __restrict__ twtab,
+                                          int twstride) {
+  Tc5Ctx& cx = tc5_ctx();
+  const uint32_t ntiles = blockDim.x / 128;
+  const uint32_t abytes = ntiles * 16384u;
+  const uint32_t base = (smem_u32(smem_ab) + 1023u) & ~1023u;  // 1 KB slack reserved
+  const uint32_t bbase = base + abytes * (PREC == 3 ? 2u : 1u);
+  for (int i = threadIdx.x; i < 4 * 32 * 32; i += blockDim.x) {
+    const int mat = i >> 10, j = (i >> 5) & 31, kk = i & 31;  // mat: fwd hi, fwd lo, inv hi, inv lo
+    const bool inv = mat >= 2;
+    const int k = j & 15, r = kk & 15;
+    float2 w = twtab[((k * r) & 15) * (L / 16) * twstride];
+    if (inv) w.y = -w.y;
+    // rows j < 16: Yr[k] = Fr Ur - Fi Ui; rows j >= 16: Yi[k] = Fi Ur + Fr Ui
+    const float g = (j < 16) ? (kk < 16 ? w.x : -w.y) : (kk < 16 ? w.y : w.x);
+    uint32_t hi, lo;
+    tf32_split<1>(g, hi, lo);
+    const uint32_t addr = bbase + (uint32_t)(mat >> 1) * 8192u + (uint32_t)(mat & 1) * 4096u + tc5_off(j, kk);
+    asm volatile("st.shared.b32 [%0], %1;" ::"r"(addr), "r"((mat & 1) ? lo : hi) : "memory");
+  }
+  if (threadIdx.x == 0) {
+    mbar_init(mbar, 1);
+    mbar_fence_init();
+    cx.a_hi = base;
+    cx.a_lo = base + abytes;
+    cx.b_fwd_hi = bbase;
+    cx.b_fwd_lo = bbase + 4096u;
+    cx.b_inv_hi = bbase + 8192u;
+    cx.b_inv_lo = bbase + 12288u;
+    cx.mbar = smem_u32(mbar);
+    cx.phase = 0u;
+    cx.ntiles = ntiles;
+    cx.ok = 1u;
+  }
+  if (threadIdx.x < 32) tc5_alloc(smem_u32(&cx.tmem), 32u * ntiles);
+  fence_async_smem();
+  tc5_fence_before();
+  __syncthreads();
+  tc5_fence_after();
+}
+
+// Release the TMEM columns (every thread calls it, after its last tcgen05.ld).
+__device__ __forceinline__ void tc5_teardown() {
+  Tc5Ctx& cx = tc5_ctx();
+  tc5_fence_before();
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    tc5_fence_after();
+    tc5_dealloc(cx.tmem, 32u * cx.ntiles);
+  }
+}
+
 // One Stockham autosort stage (radix R, sub-transform length NS) of a
 // length-L complex DFT computed by TPF = L/E threads, E values per thread.
 // Inputs are the "natural" layout (thread t holds x[t + m*TPF], m =
@@ -343,7 +627,8 @@ struct FFTStages {
     constexpr bool LAST = (NS * R == L);
     constexpr bool TC = (PREC != 0 && R == 16 && E == 16 && !WARP);
     if constexpr (TC) {
-      tc_radix16_stage<L, NS, INV, TWS, PREC>(v, sb, t, twtab, twstride);
+      if constexpr (PREC >= 3) tc5_radix16_stage<L, NS, INV, TWS, PREC>(v, sb, t, twtab, twstride);
+      else tc_radix16_stage<L, NS, INV, TWS, PREC>(v, sb, t, twtab, twstride);
       fft_sync<WARP>();
 #pragma unroll
       for (int m = 0; m < E; ++m) v[m] = sb[spad(t + m * TPF)];
@@ -521,56 +806,6 @@ __device__ __forceinline__ void r2c_post(float2 (&v)[E], float2* sb, int t,
   }
   fft_sync<WARP>();
 }
-
-// ---------------------------------------------------------------- TMA bulk copies
-// 1D bulk copies global -> shared (cp.async.bulk) completed on an mbarrier.
-// Addresses and sizes must be multiples of 16 bytes.
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-// make barrier initialisation visible to the async (TMA) proxy
-__device__ __forceinline__ void mbar_fence_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-// Bounded wait for phase `phase` of the barrier; false if it gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, int max_tries) {
-  for (int i = 0; i < max_tries; ++i) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(phase)
-        : "memory");
-    if (ok) return true;
-  }
-  return false;
-}
-// try_wait already suspends for a hardware-chosen interval per attempt; this
-// many attempts is far beyond the microseconds a bulk copy takes.
-constexpr int WF_WAIT_TRIES = 1 << 20;
-
-// Ampere-style asynchronous copies (16 or 8 bytes per thread) for strided tiles.
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async8(void* dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // ---------------------------------------------------------------- state
 // Device-resident solver state.  Problem constants are written by the setup

@@ -149,6 +149,7 @@ int check_plan_args(int ny, int nx, unsigned parts, const wf_params* p);
 int launch_col_pass_tc(int L, int mode, const ColArgs& a, cudaStream_t s);
 int launch_col_dft_tc(int inverse, const ColArgs& a, cudaStream_t s);
 bool col_tc_supported(int L);
+bool col_tc5_supported(int L);  // tcgen05 stages (dft_precision 3, 4)
 // values per thread of the row / column pass shape `variant` for a length
 int row_pass_e(int M, int variant);
 int col_pass_e(int L, int variant);

@@ -73,7 +73,7 @@ def test_plan_create_rejects_bad_params(lib):
     for kw in (dict(theta=(0.9, 1.5, 1.0)), dict(split_f=0.5, split_fp=0.5, merge_2df=0), dict(split_f=1.01, split_fp=0.0), dict(split_f=0.6, split_fp=0.6),
                dict(residual_every=0), dict(tol_u_scale=0.0), dict(refine=-1), dict(refine=9),
                dict(refine_max_iters=-1), dict(refine_lam1_iters=-1), dict(stall_checks=-1),
-               dict(autotune=3), dict(dft_precision=-1), dict(dft_precision=3),
+               dict(autotune=3), dict(dft_precision=-1), dict(dft_precision=5), dict(sweep_kernel=2),
                dict(refine_extra=-1), dict(refine_extra=9)):
         p = wf.make_params(**kw)
         h = C.c_void_p()
@@ -82,6 +82,8 @@ def test_plan_create_rejects_bad_params(lib):
 
 @pytest.mark.parametrize("ny,kw", [
     (256, dict(dft_precision=1)),                 # no 16-value column shape at 256
+    (2048, dict(dft_precision=3)),                # tcgen05 stages: columns of 512 and 1024 only
+    (4096, dict(dft_precision=4)),
     (1536, dict(dft_precision=2)),                # 3 * 2^k columns
     (1024, dict(dft_precision=1, merge_2df=0, split_fp=0.3)),  # plain sweep (stored t_2DF)
 ])

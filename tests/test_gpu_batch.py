@@ -114,7 +114,7 @@ def test_persistent_batch_matches_the_oracle_sweep_for_sweep(wf, shape_choice):
     sched = wf.make_schedule("fixed", lam, its)
     rc, stats, outs = _batch_solve(wf, probs, 0, sched, 0.0, residual_every=10, max_iters=60,
                                    autotune=shape_choice)
-    assert rc == wf.WF_ENOCONV  # tol = 0: every map runs to max_iters
+    assert rc == wf.WF_OK  # tol = 0: every map runs to max_iters, no stop test
     for p, st, s in zip(probs, stats, outs):
         assert st["iters"] == 60 and st["lam_final"] == 1.0, st
         r = O.messenger_solve(p, schedule=O.fixed_schedule(lam, its), n_iters=60, residual_every=10,
@@ -148,9 +148,9 @@ def test_persistent_batch_maps_stop_on_their_own_test(wf):
     probs = [synth.make_problem(n, n, 4300 + i, amp_jitter=0.5, k_knee=4.0, k_knee_x=4.0)
              for i, n in enumerate(sizes)]
     sched = wf.make_schedule("fixed", O.cooling_levels(1e2, 5), [40] * 5)
-    kw = dict(residual_every=10, max_iters=20000, tol_u_scale=50.0, autotune=0)
-    rc, stats, outs = _batch_solve(wf, probs, 0, sched, 3e-5, **kw)
-    _, stats1, outs1 = _batch_solve(wf, probs, 1, sched, 3e-5, **kw)
+    kw = dict(residual_every=10, max_iters=20000, tol_u_scale=5.0, autotune=0)
+    rc, stats, outs = _batch_solve(wf, probs, 0, sched, 2e-4, **kw)
+    _, stats1, outs1 = _batch_solve(wf, probs, 1, sched, 2e-4, **kw)
     assert rc == wf.WF_OK, stats
     for p, a, b, sa, sb in zip(probs, outs, outs1, stats, stats1):
         assert sa["status"] == 0 and abs(sa["iters"] - sb["iters"]) <= 10, (p.shape, sa, sb)
