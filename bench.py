@@ -342,6 +342,20 @@ def large_leg(wf, torch, peak):
             "algorithmic_bytes": {"row_pass": rb, "col_pass": cb}}
 
 
+def write_trace(wf, torch, prob, path):
+    """One headline solve with the per-checkpoint trace on (residual and
+    chi^2_aug at every checkpoint), written as JSON lines."""
+    dv = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    plan = wf.Plan(N, N, wf.parts_of(prob), solver_params(wf, trace=2))
+    out = torch.empty(N, N, device="cuda")
+    _, st = plan.solve(*[dv(a) for a in (prob.d, prob.pixel_var, prob.mask, prob.C, prob.P1f, prob.Pst,
+                                         prob.stripe_amp2)], solver_schedule(wf), TOL, out=out)
+    with open(path, "w") as f:
+        for r in plan.trace():
+            f.write(json.dumps(r) + "\n")
+    plan.close()
+
+
 def run_gpu(args):
     import torch
     ws, rank, local = _dist()
@@ -487,6 +501,8 @@ def run_gpu(args):
             "gpu_launches": launches, "clocks": clk}
     if large is not None:
         line["large_map"] = large
+    if rank == 0 and args.trace:
+        write_trace(wf, torch, prob, args.trace)
     if rank == 0:
         print(json.dumps(line))
     plan.close()
@@ -793,6 +809,9 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-large", action="store_true", help="skip the 4096^2 sub-record of the headline line")
+    ap.add_argument("--trace", default=None,
+                    help="write the per-checkpoint trace (lambda, residual terms, chi^2_aug) of one headline "
+                         "solve to this JSONL file (outside the timed region)")
     ap.add_argument("--workload", default="headline", choices=["headline", "batch", "passes", "warm", "precision"])
     ap.add_argument("--size", type=int, default=N, help="map side for --workload passes")
     ap.add_argument("--autotune", type=int, default=1, choices=[0, 1, 2],

@@ -203,6 +203,12 @@ typedef struct {
  *                  form measured slower at 1024^2 (its two grid barriers cost
  *                  more than the launch boundaries they replace), so it is
  *                  not the default.
+ *  trace           per-checkpoint trace of the iteration (wf_get_trace): 0
+ *                  (default) off; 1 lambda and the two residual terms at every
+ *                  checkpoint (a fixed schedule then evaluates the residual at
+ *                  every checkpoint, not only at lambda = 1); 2 also chi^2_aug
+ *                  (wf_chi2_aug) at every checkpoint (merged 2DF block only,
+ *                  WF_EUNSUPPORTED otherwise).  Up to 8192 records per problem.
  */
 typedef struct {
   double theta[3];
@@ -223,6 +229,7 @@ typedef struct {
   int dft_precision;
   int refine_extra;
   int sweep_kernel;
+  int trace;
 } wf_params;
 
 /* Results of a solve. */
@@ -386,6 +393,18 @@ WF_API int wf_plan_shapes(wf_plan_t plan, int* row_values, int* col_values);
  */
 WF_API int wf_time_passes(wf_plan_t plan, double lam, int n, double* us_row,
                           double* us_col);
+
+/*
+ * wf_get_trace -- the per-checkpoint trace (wf_params.trace) of every run since
+ * the plan last loaded a problem: the first solve and, after wf_solve with
+ * refine > 0, its corrections (Sec. 3.3 and Fig. 3 follow the same
+ * quantities).  *n_out receives the number of records; min(n, max_records)
+ * are written to out (host or device), 6 doubles each: sweeps done in that
+ * run, lambda of those sweeps, ||Delta d_u|| / ||d_u||, ||(S^-1 s)_m|| /
+ * ||S^-1 s||, chi^2_aug (trace = 2; NaN otherwise), and the run's index (0
+ * the first solve, 1, 2, ... its corrections).  WF_EINVAL if tracing is off.
+ */
+WF_API int wf_get_trace(wf_plan_t plan, double* out, int max_records, int* n_out);
 
 /*
  * wf_time_sweeps -- measurement aid: at fixed lambda, capture n sweeps as the

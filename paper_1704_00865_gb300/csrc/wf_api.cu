@@ -46,6 +46,9 @@ struct wf_plan_s {
   double* part = nullptr;
   double* chi = nullptr;  // wf_chi2_aug: partial sums, then the value
   unsigned* fbar = nullptr;  // grid barrier words of the one-launch sweep
+  double* trace = nullptr;   // per-checkpoint trace records (wf_params.trace)
+  int* trace_n = nullptr;
+  int run_index = 0;         // runs since the problem was loaded
   WfState* st = nullptr;
   double* lam_sched = nullptr;
   int* it_sched = nullptr;
@@ -212,11 +215,14 @@ int wf::check_plan_args(int ny, int nx, unsigned parts, const wf_params* p) {
   if (prm.refine < 0 || prm.refine > 8 || !(prm.refine_tol_scale >= 1.0) || prm.refine_max_iters < 0 ||
       prm.refine_lam1_iters < 0 || prm.stall_checks < 0 || prm.autotune < 0 || prm.autotune > 2 ||
       prm.refine_extra < 0 || prm.refine_extra > 8 ||
-      prm.dft_precision < 0 || prm.dft_precision > 4 || prm.sweep_kernel < 0 || prm.sweep_kernel > 1)
+      prm.dft_precision < 0 || prm.dft_precision > 4 || prm.sweep_kernel < 0 || prm.sweep_kernel > 1 ||
+      prm.trace < 0 || prm.trace > 2)
     return WF_EINVAL;
   // tensor-core radix-16 stages: 16-value column shapes, merged 2DF block
   if (prm.dft_precision != 0 && (!col_tc_supported(ny) || prm.merge_2df != 1)) return WF_EUNSUPPORTED;
   if (prm.dft_precision >= 3 && !col_tc5_supported(ny)) return WF_EUNSUPPORTED;
+  // chi^2_aug is summed for the merged 2DF block (or without a 1/f part)
+  if (prm.trace == 2 && (parts & WF_PART_1F) && !prm.merge_2df) return WF_EUNSUPPORTED;
   return WF_OK;
 }
 
@@ -268,6 +274,10 @@ int wf_plan_create(wf_plan_t* out, int ny, int nx, unsigned parts, const wf_para
   AL(P->chi, (size_t)chi2_scratch(ny, nx) + 1);
   AL(P->st, (size_t)1);
   AL(P->fbar, (size_t)4);
+  if (prm.trace > 0) {
+    AL(P->trace, (size_t)WF_TRACE_CAP * WF_TRACE_FIELDS);
+    AL(P->trace_n, (size_t)1);
+  }
   AL(P->st_save, (size_t)1);
   AL(P->lam_sched, (size_t)260);
   AL(P->it_sched, (size_t)260);
@@ -505,6 +515,11 @@ static CtrlArgs ctrl_args(wf_plan_s* P) {
   c.stall = P->p.stall_checks;
   c.lam_sched = P->lam_sched;
   c.it_sched = P->it_sched;
+  c.trace = P->trace;
+  c.trace_n = P->trace_n;
+  c.trace_cap = WF_TRACE_CAP;
+  c.run_index = P->run_index;
+  c.chi_val = nullptr;
   return c;
 }
 
@@ -653,6 +668,8 @@ int wf_set_problem(wf_plan_t P, const float* d, const float* pixel_var, const ui
   a.merge = P->merge;
   CK(cudaMemsetAsync(P->st, 0, sizeof(WfState), P->stream));
   CK(cudaMemsetAsync(P->fbar, 0, 4 * sizeof(unsigned), P->stream));
+  if (P->trace_n) CK(cudaMemsetAsync(P->trace_n, 0, sizeof(int), P->stream));
+  P->run_index = 0;
   CKI(launch_setup(a, P->stream));
   P->launches += 5;
   // iteration starts from zero fields (Sec. 2)
@@ -698,6 +715,26 @@ static void fill_stats(wf_plan_s* P, wf_stats* st, int status) {
 }
 
 }  // extern "C"
+
+// the fields wf_chi2_aug sums (merged 2DF block or no 1/f part)
+static Chi2Fields chi2_fields(wf_plan_s* P) {
+  Chi2Fields f{};
+  f.ny = P->ny;
+  f.nx = P->nx;
+  f.has_rf = P->has_rf;
+  f.d0 = P->f_x;
+  f.t = P->has_rf ? P->f_t1 : P->f_y;
+  f.d1 = P->has_rf ? P->f_d1 : nullptr;
+  f.dn = P->dn;
+  f.eig = P->eig;
+  f.eig_nyq = P->eig_nyq;
+  f.pst = P->pst;
+  f.a2 = P->a2;
+  f.twx = P->twx;
+  f.twy = P->twy;
+  f.st = P->st;
+  return f;
+}
 
 // ---------------------------------------------------------------- persistent batch
 static int run_setup(wf_plan_t P, const wf_schedule* sch, double tol, CtrlArgs* out, double* lam0_out);
@@ -759,6 +796,7 @@ int wf::run_plans_persistent(const std::vector<wf_plan_t>& plans, const std::vec
     P->stream = s;
     double lam0 = 1.0;
     int rc = run_setup(P, sch, tol, &ctrl[i], &lam0);
+    P->run_index += 1;
     if (!rc) rc = launch_set_lambda(P->st, lam0, 1, s) ? WF_ECUDA : WF_OK;
     if (!rc) rc = plan_batch_map(P, variant[i], &maps[i]);
     if (rc) {
@@ -962,7 +1000,7 @@ static int run_setup(wf_plan_t P, const wf_schedule* sch, double tol, CtrlArgs* 
     CK(cudaMemcpyAsync(P->lam_sched, L.data(), L.size() * sizeof(double), cudaMemcpyHostToDevice, P->stream));
     CK(cudaMemcpyAsync(P->it_sched, I.data(), I.size() * sizeof(int), cudaMemcpyHostToDevice, P->stream));
     c.mode = 0;
-    c.skip_fixed = 1;
+    c.skip_fixed = P->p.trace ? 0 : 1;  // a trace wants the residual at every checkpoint
     c.nlevels = (int)L.size();
     lam0 = L[0];
   } else if (sch->mode == WF_SCHED_ADAPTIVE) {
@@ -990,6 +1028,9 @@ static int wf_run_on(wf_plan_t P, const wf_schedule* sch, double tol, wf_stats* 
   double lam0;
   int rc0 = run_setup(P, sch, tol, &c, &lam0);
   if (rc0) return rc0;
+  P->run_index += 1;
+  const int nchi = chi2_scratch(P->ny, P->nx);
+  if (P->p.trace == 2) c.chi_val = P->chi + nchi;  // chi^2_aug at each checkpoint, before the controller
   CKI(launch_set_lambda(P->st, lam0, 1, P->stream));
   P->launches += 1;
   const long long it0 = P->it_done;
@@ -1006,6 +1047,10 @@ static int wf_run_on(wf_plan_t P, const wf_schedule* sch, double tol, wf_stats* 
       e += R;
       rc = enqueue_residual(P, (int)(e & 1), 1);
       if (rc) return rc;
+      if (P->p.trace == 2) {
+        CKI(launch_chi2(chi2_fields(P), P->chi, P->chi + nchi, P->stream));
+        P->launches += 3;
+      }
       CKI(launch_ctrl(c, P->stream));
       P->launches += 1;
     }
@@ -1026,6 +1071,7 @@ static int wf_run_on(wf_plan_t P, const wf_schedule* sch, double tol, wf_stats* 
   put(&c.mode, 4); put(&c.nlevels, 4); put(&c.R, 4); put(&c.max_iters, 4); put(&c.count_iters, 4);
   put(&c.skip_fixed, 4);
   put(&par, 8); put(&src, 8);
+  put(&c.run_index, 4);  // stamped into trace records
   const bool use_graph = (per_chunk % 2 == 0);
   bool first = true;
   for (;;) {
@@ -1099,21 +1145,7 @@ int wf_run(wf_plan_t P, const wf_schedule* sch, double tol, wf_stats* st) {
 int wf_chi2_aug(wf_plan_t P, double* value) {
   if (!P || !P->loaded || !value) return WF_EINVAL;
   if (P->has_f && !P->merge) return WF_EUNSUPPORTED;  // the plain sweep's t_2DF links are not summed
-  Chi2Fields f{};
-  f.ny = P->ny;
-  f.nx = P->nx;
-  f.has_rf = P->has_rf;
-  f.d0 = P->f_x;
-  f.t = P->has_rf ? P->f_t1 : P->f_y;
-  f.d1 = P->has_rf ? P->f_d1 : nullptr;
-  f.dn = P->dn;
-  f.eig = P->eig;
-  f.eig_nyq = P->eig_nyq;
-  f.pst = P->pst;
-  f.a2 = P->a2;
-  f.twx = P->twx;
-  f.twy = P->twy;
-  f.st = P->st;
+  const Chi2Fields f = chi2_fields(P);
   const int n = chi2_scratch(P->ny, P->nx);
   CKI(launch_chi2(f, P->chi, P->chi + n, P->stream));
   P->launches += 3;
@@ -1566,6 +1598,24 @@ int wf_time_passes(wf_plan_t P, double lam, int n, double* us_row, double* us_co
   if (rc) return rc;
   if (us_row) *us_row = res[0];
   if (us_col) *us_col = res[1];
+  return WF_OK;
+}
+
+int wf_get_trace(wf_plan_t P, double* out, int max_records, int* n_out) {
+  if (!P || !P->trace || max_records < 0 || (!out && max_records > 0)) return WF_EINVAL;
+  int n = 0;
+  CK(cudaMemcpyAsync(&n, P->trace_n, sizeof(int), cudaMemcpyDeviceToHost, P->stream));
+  CK(cudaStreamSynchronize(P->stream));
+  n = std::min(n, WF_TRACE_CAP);
+  const int k = std::min(n, max_records);
+  if (k > 0) {
+    const int where_ = ptr_where(out);
+    if (where_ == PTR_OTHER_DEVICE) return WF_EINVAL;
+    CK(cudaMemcpyAsync(out, P->trace, (size_t)k * WF_TRACE_FIELDS * sizeof(double),
+                       where_ == PTR_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, P->stream));
+    CK(cudaStreamSynchronize(P->stream));
+  }
+  if (n_out) *n_out = n;
   return WF_OK;
 }
 

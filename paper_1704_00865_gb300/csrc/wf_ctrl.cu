@@ -338,6 +338,21 @@ __global__ void __launch_bounds__(CTRL_THREADS) ctrl_kernel(CtrlArgs a) {
   st->iter += a.R;
   st->in_level += a.R;
   st->checkpoints += 1;
+  if (a.trace != nullptr) {
+    // one record per checkpoint: sweeps, the lambda they ran at, the
+    // residual terms, chi^2_aug, the run
+    const int i = *a.trace_n;
+    if (i < a.trace_cap) {
+      double* r = a.trace + (size_t)WF_TRACE_FIELDS * i;
+      r[0] = (double)st->iter;
+      r[1] = st->lam;
+      r[2] = skipped ? nan("") : st->rel_u;
+      r[3] = skipped ? nan("") : st->rel_m;
+      r[4] = a.chi_val != nullptr ? *a.chi_val : nan("");
+      r[5] = (double)a.run_index;
+      *a.trace_n = i + 1;
+    }
+  }
   if (!skipped && a.tol > 0 && st->lam == 1.0 && st->rel_u <= a.tol_u && st->rel_m <= a.tol) {
     st->done = 1;
     st->status = 0;

@@ -310,7 +310,14 @@ struct CtrlArgs {
   int skip_fixed;             // fixed schedule: skip residuals nothing uses (st->skip_resid)
   int stall;                  // stop after this many checkpoints at lambda = 1
                               // without a 1% drop of ||Delta d_u||^2 (0: never)
+  double* trace;              // per-checkpoint records (6 doubles each) or nullptr
+  int* trace_n;               // records written so far
+  int trace_cap;
+  int run_index;              // stamped into the records
+  const double* chi_val;      // chi^2_aug of this checkpoint (trace = 2) or nullptr
 };
+constexpr int WF_TRACE_CAP = 8192;
+constexpr int WF_TRACE_FIELDS = 6;
 int launch_ctrl(const CtrlArgs& a, cudaStream_t s);
 int launch_set_lambda(WfState* st, double lam, int reset, cudaStream_t s);
 // refinement helpers: dn_out = (rho, Nbar of dn_in) per pixel and ||rho_u||^2

@@ -26,7 +26,7 @@ WF_FIELD_S, WF_FIELD_T_2DF, WF_FIELD_D_2DF, WF_FIELD_T_RF, WF_FIELD_D_RF = range
 # every symbol include/wf.h declares
 EXPORTS = ["wf_version", "wf_strerror", "wf_params_default", "wf_plan_create", "wf_plan_destroy",
            "wf_set_problem", "wf_run", "wf_iterate", "wf_residual", "wf_chi2_aug", "wf_get_field", "wf_solve",
-           "wf_fft2", "wf_launch_count", "wf_time_passes", "wf_time_sweeps", "wf_fft2_noalloc",
+           "wf_fft2", "wf_launch_count", "wf_time_passes", "wf_time_sweeps", "wf_get_trace", "wf_fft2_noalloc",
            "wf_batch_create", "wf_batch_destroy", "wf_batch_solve", "wf_batch_launch_count",
            "wf_fno_create", "wf_fno_destroy", "wf_fno_num_params", "wf_fno_forward", "wf_fno_gradient",
            "wf_fno_train_step", "wf_fno_get_params", "wf_fno_features", "wf_solve_warm", "wf_plan_shapes",
@@ -45,7 +45,8 @@ class wf_params(C.Structure):
                 ("check_every", C.c_int), ("merge_2df", C.c_int), ("refine", C.c_int),
                 ("refine_tol_scale", C.c_double), ("refine_max_iters", C.c_int),
                 ("refine_lam1_iters", C.c_int), ("stall_checks", C.c_int), ("autotune", C.c_int),
-                ("dft_precision", C.c_int), ("refine_extra", C.c_int), ("sweep_kernel", C.c_int)]
+                ("dft_precision", C.c_int), ("refine_extra", C.c_int), ("sweep_kernel", C.c_int),
+                ("trace", C.c_int)]
 
 
 class wf_stats(C.Structure):
@@ -106,6 +107,7 @@ def load(path: Optional[str] = None):
     L.wf_launch_count.argtypes = [vp]
     L.wf_time_passes.argtypes = [vp, C.c_double, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.wf_time_sweeps.argtypes = [vp, C.c_double, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int)]
+    L.wf_get_trace.argtypes = [vp, vp, C.c_int, C.POINTER(C.c_int)]
     L.wf_fft2_noalloc.argtypes = [C.c_int, C.c_int, vp, vp, C.c_int, vp]
     L.wf_batch_create.argtypes = [C.POINTER(vp), C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_uint,
                                   C.POINTER(wf_params), C.c_int, vp]
@@ -183,8 +185,10 @@ def make_params(theta=None, split_f=None, split_w=None, residual_every=None, max
                 check_every=None, merge_2df=None, tol_u_scale=None, split_fp=None,
                 refine=None, refine_tol_scale=None, refine_max_iters=None,
                 refine_lam1_iters=None, stall_checks=None, autotune=None,
-                dft_precision=None, refine_extra=None, sweep_kernel=None) -> wf_params:
+                dft_precision=None, refine_extra=None, sweep_kernel=None, trace=None) -> wf_params:
     p = wf_params_default()
+    if trace is not None:
+        p.trace = int(trace)
     if sweep_kernel is not None:
         p.sweep_kernel = int(sweep_kernel)
     if refine_extra is not None:
@@ -393,6 +397,17 @@ class Plan:
         r, c = C.c_int(), C.c_int()
         _check(load().wf_plan_shapes(self.h, C.byref(r), C.byref(c)), "wf_plan_shapes")
         return r.value, c.value
+
+    def trace(self):
+        """Per-checkpoint records of the runs since the last load (wf_get_trace):
+        a list of dicts with sweeps, lam, rel_rho_u, rel_rho_m, chi2_aug, run."""
+        n = C.c_int()
+        _check(load().wf_get_trace(self.h, None, 0, C.byref(n)), "wf_get_trace")
+        buf = np.empty((max(n.value, 1), 6), np.float64)
+        _check(load().wf_get_trace(self.h, C.c_void_p(buf.ctypes.data), n.value, C.byref(n)), "wf_get_trace")
+        keys = ("sweeps", "lam", "rel_rho_u", "rel_rho_m", "chi2_aug", "run")
+        return [{k: (int(v) if k in ("sweeps", "run") else float(v)) for k, v in zip(keys, row)}
+                for row in buf[:n.value]]
 
     def time_sweeps(self, lam: float, n: int):
         """Mean CUDA-event time (us) of one sweep as the plan launches it, and

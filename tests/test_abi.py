@@ -51,7 +51,7 @@ def test_host_only_entry_points(lib):
     assert p.residual_every == 10 and p.check_every == 8
     assert p.merge_2df == 1 and p.tol_u_scale == 1.0 and p.refine == 0 and p.refine_tol_scale == 100.0
     assert p.autotune == 1 and p.stall_checks == 0 and p.refine_max_iters == 0
-    assert p.dft_precision == 0 and p.refine_extra == 0 and p.sweep_kernel == 0
+    assert p.dft_precision == 0 and p.refine_extra == 0 and p.sweep_kernel == 0 and p.trace == 0
     assert lib.wf_plan_shapes(None, None, None) == wf.WF_EINVAL
 
 
@@ -73,7 +73,7 @@ def test_plan_create_rejects_bad_params(lib):
     for kw in (dict(theta=(0.9, 1.5, 1.0)), dict(split_f=0.5, split_fp=0.5, merge_2df=0), dict(split_f=1.01, split_fp=0.0), dict(split_f=0.6, split_fp=0.6),
                dict(residual_every=0), dict(tol_u_scale=0.0), dict(refine=-1), dict(refine=9),
                dict(refine_max_iters=-1), dict(refine_lam1_iters=-1), dict(stall_checks=-1),
-               dict(autotune=3), dict(dft_precision=-1), dict(dft_precision=5), dict(sweep_kernel=2),
+               dict(autotune=3), dict(dft_precision=-1), dict(dft_precision=5), dict(sweep_kernel=2), dict(trace=3),
                dict(refine_extra=-1), dict(refine_extra=9)):
         p = wf.make_params(**kw)
         h = C.c_void_p()
