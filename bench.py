@@ -134,7 +134,7 @@ def problem():
 
 
 # the sources each timed kernel is built from
-KERNEL_SOURCES = {"row_pass": ["wf_rows.cu", "wf_device.cuh"],
+KERNEL_SOURCES = {"row_pass": ["wf_rows.cu", "wf_rows_common.cuh", "wf_device.cuh"],
                   "col_pass": ["wf_colpass.cuh", "wf_colpass.cu", "wf_cols_common.cuh", "wf_device.cuh"]}
 
 

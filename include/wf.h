@@ -402,7 +402,11 @@ WF_API int wf_time_passes(wf_plan_t plan, double lam, int n, double* us_row,
  * are written to out (host or device), 6 doubles each: sweeps done in that
  * run, lambda of those sweeps, ||Delta d_u|| / ||d_u||, ||(S^-1 s)_m|| /
  * ||S^-1 s||, chi^2_aug (trace = 2; NaN otherwise), and the run's index (0
- * the first solve, 1, 2, ... its corrections).  WF_EINVAL if tracing is off.
+ * the first solve, 1, 2, ... its corrections).  The residual terms and
+ * chi^2_aug of a correction are those of its own problem (data Delta d_u);
+ * its objective also has the masked-pixel source term, which chi^2_aug does
+ * not include, so only the first solve's chi^2_aug is monotone within a
+ * lambda level.  WF_EINVAL if tracing is off.
  */
 WF_API int wf_get_trace(wf_plan_t plan, double* out, int max_records, int* n_out);
 

@@ -1071,7 +1071,7 @@ static int wf_run_on(wf_plan_t P, const wf_schedule* sch, double tol, wf_stats* 
   put(&c.mode, 4); put(&c.nlevels, 4); put(&c.R, 4); put(&c.max_iters, 4); put(&c.count_iters, 4);
   put(&c.skip_fixed, 4);
   put(&par, 8); put(&src, 8);
-  put(&c.run_index, 4);  // stamped into trace records
+  if (P->p.trace) put(&c.run_index, 4);  // stamped into trace records
   const bool use_graph = (per_chunk % 2 == 0);
   bool first = true;
   for (;;) {

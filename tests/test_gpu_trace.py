@@ -28,7 +28,7 @@ def test_trace_records_every_checkpoint(wf):
     tr = plan.trace()
     assert [r["sweeps"] for r in tr] == [10, 20, 30, 40, 50, 60]
     assert [r["lam"] for r in tr] == [30.0, 30.0, 3.0, 3.0, 1.0, 1.0]
-    assert all(r["run"] == 1 for r in tr)
+    assert all(r["run"] == 0 for r in tr)
     # the last record is the state the plan holds: its residual and chi^2_aug
     u, m = plan.residual()
     assert tr[-1]["rel_rho_u"] == pytest.approx(u, rel=1e-12) and tr[-1]["rel_rho_m"] == pytest.approx(m, rel=1e-12)
@@ -52,8 +52,8 @@ def test_trace_of_a_refined_solve_and_without_chi2(wf):
     _, st = plan.solve(*[dev(a) for a in (prob.d, prob.pixel_var, prob.mask, prob.C, prob.P1f, prob.Pst,
                                           prob.stripe_amp2)], wf.make_schedule("fixed", [10.0], [20]), 0.0, out=out)
     tr = plan.trace()
-    assert [r["run"] for r in tr] == [1] * 4 + [2] * 3 + [3] * 3
-    assert sum(1 for r in tr if r["run"] > 1) * 10 == st["iters"] - 40
+    assert [r["run"] for r in tr] == [0] * 4 + [1] * 3 + [2] * 3
+    assert sum(1 for r in tr if r["run"] > 0) * 10 == st["iters"] - 40
     assert all(math.isnan(r["chi2_aug"]) for r in tr)
     assert all(np.isfinite(r["rel_rho_u"]) for r in tr)
     plan.close()
