@@ -47,9 +47,33 @@ struct BShape {
   static constexpr int SP = SPad<L>::size;
   static constexpr int WANT = (W >= 32) ? 1 : (16 / W) % 16;
   static constexpr int STRIDE = SP + ((WANT - SP % 16) + 16) % 16;
-  static constexpr size_t row_smem = (size_t)ROWS * SPad<M>::size * 8;
-  static constexpr size_t col_smem = (size_t)W * STRIDE * 8;
+  // Items whose inputs fit in shared memory beside their transform buffers
+  // (two CTAs per SM) stage them first, all copies in flight at once: rows
+  // of 8 values per thread (d_RF and the pixel table by bulk copies, t_RF
+  // and d_2DF by 16-byte copies), columns up to 16 values per thread (the
+  // messenger and (C, P1f) tiles).  The others load at the point of use.
+  static constexpr bool ROW_STAGED = (RE == 8);
+  static constexpr bool COL_STAGED = (CE <= 16) && (W >= 2);
+  static constexpr bool COL_TILED = (W % WF_TW == 0);
+  static constexpr size_t rows_in = (size_t)ROWS * M;  // complex values per row field
+  static constexpr size_t row_fft = (size_t)ROWS * SPad<M>::size * 8;
+  static constexpr size_t row_smem = row_fft + (ROW_STAGED ? rows_in * (8 + 16 + 8 + 8) : 0);
+  static constexpr size_t col_tile = (size_t)W * L * 8;
+  static constexpr size_t col_fft = (size_t)W * STRIDE * 8;
+  static constexpr size_t col_smem = col_fft + (COL_STAGED ? 2 * col_tile : 0);
   static constexpr size_t smem = row_smem > col_smem ? row_smem : col_smem;
+  // position of (ky, column c of the item) in a staged tile
+  static __device__ __forceinline__ int sidx(int ky, int c) {
+    if constexpr (COL_TILED) return (c / WF_TW) * L * WF_TW + ky * WF_TW + (c % WF_TW);
+    else return ky * W + c;
+  }
+};
+
+// Per-CTA staging state: the bulk-copy mbarrier and its next phase.
+struct BatchStage {
+  uint64_t* bar;
+  uint32_t phase;
+  bool ok;
 };
 
 // sizes in class order; class = 2 * (index of the size) + shape
@@ -94,20 +118,106 @@ __device__ __forceinline__ void batch_row_item(const BatchMapArgs& m, int grp, f
   }
 }
 
+// The row item with its inputs staged (ROW_STAGED shapes): the same
+// arithmetic as batch_row_item, reading from shared memory.
+template <int N, int V>
+__device__ __forceinline__ void batch_row_item_staged(const BatchMapArgs& m, int grp, float2* sm, BatchStage& bs) {
+  using S = BShape<N, V>;
+  constexpr int M = S::M, E = S::RE, TPF = S::TPF, ROWS = S::ROWS;
+  float2* s_fft = sm;
+  float2* s_d1 = sm + S::row_fft / 8;
+  float4* s_dn = reinterpret_cast<float4*>(s_d1 + S::rows_in);
+  float2* s_t1 = reinterpret_cast<float2*>(s_dn + S::rows_in);
+  float2* s_x = s_t1 + S::rows_in;
+  const int g = threadIdx.x / TPF, t = threadIdx.x - g * TPF;
+  const int y0 = grp * ROWS, y = y0 + g;
+  const size_t row0 = (size_t)y * M;
+  float2* sb = s_fft + g * SPad<M>::size;
+  if (threadIdx.x == 0) {
+    // d_RF was written by other CTAs' generic stores earlier in the launch
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    mbar_expect_tx(bs.bar, (uint32_t)(S::rows_in * (8 + 16)));
+    bulk_g2s(s_d1, m.f_d1 + (size_t)y0 * M, (uint32_t)(S::rows_in * 8), bs.bar);
+    bulk_g2s(s_dn, m.dn + (size_t)y0 * M, (uint32_t)(S::rows_in * 16), bs.bar);
+  }
+  for (int i = threadIdx.x; i < ROWS * (M / 2); i += BT) {
+    const int r = i / (M / 2);
+    const int k = (i - r * (M / 2)) * 2;
+    cp_async16(s_t1 + r * M + k, m.f_t1 + tidx(y0 + r, k, N));
+    cp_async16(s_x + r * M + k, m.f_x + tidx(y0 + r, k, N));
+  }
+  cp_async_commit();
+  const float T2 = m.st->Tf[2], T1 = m.st->Tf[1], off1 = (float)m.st->off[1];
+  const float a2y = (m.a2 != nullptr) ? __ldg(&m.a2[y]) : 1.f;
+  const float pkn = __ldg(&m.pst[M]);
+  if (!mbar_wait(bs.bar, bs.phase, WF_WAIT_TRIES)) bs.ok = false;
+  bs.phase ^= 1u;
+  float2 v[E];
+#pragma unroll
+  for (int k = 0; k < E; ++k) v[k] = s_d1[g * M + t + k * TPF];
+  c2r_pre<M, E>(v, sb, t, m.twx);
+  fft_block<M, E, true>(v, sb, t, m.twh, 1);
+#pragma unroll
+  for (int k = 0; k < E; ++k) {
+    const float4 q = s_dn[g * M + t + k * TPF];
+    v[k] = make_float2(tpx_update(q.x, q.y, v[k].x, T2), tpx_update(q.z, q.w, v[k].y, T2));
+  }
+  fft_block<M, E, false>(v, sb, t, m.twh, 1);
+  r2c_post<M, E>(v, sb, t, m.twx);
+  cp_async_wait<0>();
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < E; ++k) {
+    const int kk = t + k * TPF;
+    float2 d1, t1;
+    stripe_update(kk, v[k], s_t1[g * M + kk], s_x[g * M + kk], a2y, __ldg(&m.pst[kk]), pkn, off1, T2, T1, d1, t1);
+    m.f_d1[row0 + kk] = d1;
+    m.f_t1[tidx(y, kk, N)] = t1;
+  }
+}
+
 // The column pass of W columns of one map (the merged 2DF block between the
 // forward and inverse column DFTs; with the defect-correction source when
 // the map has one).
 template <int N, int V>
-__device__ __forceinline__ void batch_col_item(const BatchMapArgs& m, int grp, float2* sm) {
+__device__ __forceinline__ void batch_col_item(const BatchMapArgs& m, int grp, float2* sm, BatchStage& bs) {
   using S = BShape<N, V>;
   constexpr int L = S::L, E = S::CE, TPC = S::TPC, W = S::W;
   const int c = threadIdx.x % W, tc = threadIdx.x / W;
   const int col0 = grp * W, col = col0 + c;
   float2* sb = sm + c * S::STRIDE;
+  float2* s_y = sm + S::col_fft / 8;
+  float2* s_eig = s_y + S::col_tile / 8;
   const float Tl = m.st->Tf[1], off0 = (float)m.st->off[0];
   float2 u[E];
+  if constexpr (S::COL_STAGED) {
+    // the messenger tile (written by other CTAs earlier in the launch) and
+    // the (C, P1f) tile
+    if constexpr (S::COL_TILED) {
+      if (threadIdx.x == 0) {
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        mbar_expect_tx(bs.bar, (uint32_t)(2 * S::col_tile));
+        bulk_g2s(s_y, m.f_t1 + tidx(0, col0, N), (uint32_t)S::col_tile, bs.bar);
+        bulk_g2s(s_eig, m.eig + tidx(0, col0, N), (uint32_t)S::col_tile, bs.bar);
+      }
+      if (!mbar_wait(bs.bar, bs.phase, WF_WAIT_TRIES)) bs.ok = false;
+      bs.phase ^= 1u;
+    } else {
+      static_assert(S::COL_TILED || W == 2, "half-tile items are two columns wide");
+      for (int ky = threadIdx.x; ky < L; ky += BT) {
+        cp_async16(s_y + ky * 2, m.f_t1 + tidx(ky, col0, N));
+        cp_async16(s_eig + ky * 2, m.eig + tidx(ky, col0, N));
+      }
+      cp_async_commit();
+      cp_async_wait<0>();
+      __syncthreads();
+    }
 #pragma unroll
-  for (int k = 0; k < E; ++k) u[k] = __ldcg(&m.f_t1[tidx(tc + k * TPC, col, N)]);
+    for (int k = 0; k < E; ++k) u[k] = s_y[S::sidx(tc + k * TPC, c)];
+  } else {
+#pragma unroll
+    for (int k = 0; k < E; ++k) u[k] = __ldcg(&m.f_t1[tidx(tc + k * TPC, col, N)]);
+  }
   fft_block<L, E, false>(u, sb, tc, m.twy, 1);
   // partner values Z[-k] for the packed column 0, read from the exchange
   // buffer (first group only; uniform)
@@ -120,7 +230,9 @@ __device__ __forceinline__ void batch_col_item(const BatchMapArgs& m, int grp, f
 #pragma unroll
   for (int k = 0; k < E; ++k) {
     const int ky = tc + k * TPC;
-    const float2 eg = __ldg(&m.eig[tidx(ky, col, N)]);
+    float2 eg;
+    if constexpr (S::COL_STAGED) eg = s_eig[S::sidx(ky, c)];
+    else eg = __ldg(&m.eig[tidx(ky, col, N)]);
     const float2 egb = packed ? __ldg(&m.eig_nyq[ky]) : eg;
     const float2 vp = packed ? sb[spad(neg_mod<L>(ky))] : u[k];
     if (m.src != nullptr) {
@@ -139,25 +251,29 @@ __device__ __forceinline__ void batch_col_item(const BatchMapArgs& m, int grp, f
 }
 
 template <int N, int V>
-__device__ __forceinline__ void batch_item(int phase, const BatchMapArgs& m, int grp, float2* sm) {
-  if (phase == 0) batch_row_item<N, V>(m, grp, sm);
-  else batch_col_item<N, V>(m, grp, sm);
+__device__ __forceinline__ void batch_item(int phase, const BatchMapArgs& m, int grp, float2* sm, BatchStage& bs) {
+  if (phase == 0) {
+    if constexpr (BShape<N, V>::ROW_STAGED) batch_row_item_staged<N, V>(m, grp, sm, bs);
+    else batch_row_item<N, V>(m, grp, sm);
+  } else {
+    batch_col_item<N, V>(m, grp, sm, bs);
+  }
 }
 
-__device__ __forceinline__ void batch_dispatch(int phase, const BatchMapArgs& m, int grp, float2* sm) {
+__device__ __forceinline__ void batch_dispatch(int phase, const BatchMapArgs& m, int grp, float2* sm, BatchStage& bs) {
   switch (m.cls) {
-    case 0: batch_item<256, 0>(phase, m, grp, sm); break;
-    case 1: batch_item<256, 1>(phase, m, grp, sm); break;
-    case 2: batch_item<384, 0>(phase, m, grp, sm); break;
-    case 4: batch_item<512, 0>(phase, m, grp, sm); break;
-    case 5: batch_item<512, 1>(phase, m, grp, sm); break;
-    case 6: batch_item<768, 0>(phase, m, grp, sm); break;
-    case 8: batch_item<1024, 0>(phase, m, grp, sm); break;
-    case 9: batch_item<1024, 1>(phase, m, grp, sm); break;
-    case 10: batch_item<1536, 0>(phase, m, grp, sm); break;
-    case 11: batch_item<1536, 1>(phase, m, grp, sm); break;
-    case 12: batch_item<2048, 0>(phase, m, grp, sm); break;
-    case 13: batch_item<2048, 1>(phase, m, grp, sm); break;
+    case 0: batch_item<256, 0>(phase, m, grp, sm, bs); break;
+    case 1: batch_item<256, 1>(phase, m, grp, sm, bs); break;
+    case 2: batch_item<384, 0>(phase, m, grp, sm, bs); break;
+    case 4: batch_item<512, 0>(phase, m, grp, sm, bs); break;
+    case 5: batch_item<512, 1>(phase, m, grp, sm, bs); break;
+    case 6: batch_item<768, 0>(phase, m, grp, sm, bs); break;
+    case 8: batch_item<1024, 0>(phase, m, grp, sm, bs); break;
+    case 9: batch_item<1024, 1>(phase, m, grp, sm, bs); break;
+    case 10: batch_item<1536, 0>(phase, m, grp, sm, bs); break;
+    case 11: batch_item<1536, 1>(phase, m, grp, sm, bs); break;
+    case 12: batch_item<2048, 0>(phase, m, grp, sm, bs); break;
+    case 13: batch_item<2048, 1>(phase, m, grp, sm, bs); break;
     default: break;
   }
 }
@@ -171,18 +287,39 @@ constexpr size_t cmax(size_t a, size_t b) { return a > b ? a : b; }
 constexpr size_t kBatchSmem =
     cmax(cmax(cmax(bsm2<256>(), BShape<384, 0>::smem), cmax(bsm2<512>(), BShape<768, 0>::smem)),
          cmax(cmax(bsm2<1024>(), bsm2<1536>()), bsm2<2048>()));
+// two CTAs per SM: 228 KB of shared memory less 1 KB reserved per CTA and
+// the static words
+static_assert(kBatchSmem <= 112 * 1024, "two batch CTAs fit on an SM");
 
 __global__ void __launch_bounds__(BT, 2) batch_sweep_kernel(BatchArgs a) {
   extern __shared__ __align__(16) float2 bsm[];
   __shared__ int s_item, s_ok;
+  __shared__ __align__(8) uint64_t s_bar;
   unsigned nbar = 0;
+  if (threadIdx.x == 0) {
+    mbar_init(&s_bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  BatchStage bs{&s_bar, 0u, true};
   for (int it = 0; it < a.nsweeps; ++it) {
     for (int phase = 0; phase < 2; ++phase) {
       const int nitems = phase ? a.n_col : a.n_row;
       const int2* items = phase ? a.col_items : a.row_items;
       unsigned* q = a.queue + 2 * it + phase;
       for (;;) {
-        __syncthreads();  // the last item's shared memory and s_item are free
+        // the last item's shared memory and s_item are free; a staging copy
+        // that did not land within its bounded wait ends the launch (the
+        // other CTAs leave at their next grid barrier)
+        if (__syncthreads_or(bs.ok ? 0 : 1)) {
+          if (threadIdx.x == 0) {
+            atomicOr(a.err, WF_ERR_TIMEOUT);
+            atomicExch(&a.bar[2], 1u);
+            mbar_wait(bs.bar, bs.phase ^ 1u, WF_WAIT_TRIES);  // the copy still in flight
+          }
+          __syncthreads();
+          return;
+        }
         if (threadIdx.x == 0) s_item = (int)atomicAdd(q, 1u);
         __syncthreads();
         const int k = s_item;
@@ -190,8 +327,10 @@ __global__ void __launch_bounds__(BT, 2) batch_sweep_kernel(BatchArgs a) {
         const int2 w = items[k];
         const BatchMapArgs m = a.maps[w.x];
         if (m.st->done) continue;  // uniform: written between launches only
-        batch_dispatch(phase, m, w.y, bsm);
+        batch_dispatch(phase, m, w.y, bsm, bs);
       }
+      // the stores of this phase, seen by the next phase's bulk copies
+      asm volatile("fence.proxy.async.global;" ::: "memory");
       if ((phase == 0 || it + 1 < a.nsweeps) && !grid_barrier(a.bar, ++nbar * gridDim.x, &s_ok, a.err)) return;
     }
   }
