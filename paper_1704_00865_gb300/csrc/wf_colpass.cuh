@@ -149,6 +149,14 @@ col_pass_kernel(ColArgs a) {
   if constexpr (Cfg::TWS)
     if (threadIdx.x == 0) bulk_g2s(s_tw, a.twy, (uint32_t)(L * 8), &bar[1]);
   cp_async_commit();
+  // Maps above L2: the CTA that will run on this SM one wave later (pf CTAs
+  // on) finds its tiles in L2 -- (C, P1f) now, the messenger once the
+  // previous kernel is done.  Half-tile CTAs hint the whole tile from the
+  // first CTA of the tile.
+  const int nb = blockIdx.x + a.pf;
+  const bool pf = a.pf > 0 && nb < (int)gridDim.x && threadIdx.x == 0 && (Cfg::TILED || (nb * W) % WF_TW == 0);
+  constexpr size_t pf_bytes = (size_t)L * (Cfg::TILED ? W : WF_TW) * 8;
+  if (pf) prefetch_l2_range(a.eig + tidx(0, nb * W, a.ny), pf_bytes);
   // (C, P1f) at kx = nx/2 for the packed column (fixed during a solve)
   const bool packed = (blockIdx.x == 0 && c == 0);
   float2 egn[E];
@@ -165,6 +173,10 @@ col_pass_kernel(ColArgs a) {
   if constexpr (Cfg::SRC) stage_tiled<L, MODE, EV>(s_t0, a.src, col0, a.ny, &bar[0]);
   if constexpr (Cfg::T0) tile_load_rowmajor<L, W, Cfg::THREADS>(s_t0, a.f_t0, col0, ncols);
   cp_async_commit();
+  if (pf) {
+    prefetch_l2_range(a.f_y + tidx(0, nb * W, a.ny), pf_bytes);
+    if constexpr (Cfg::SRC) prefetch_l2_range(a.src + tidx(0, nb * W, a.ny), pf_bytes);
+  }
   // link covariances of this lambda level (written by the controller)
   const float Tl = a.has_rf ? a.st->Tf[1] : a.st->Tf[2];  // link to the RF/PX messenger
   const float off0 = (float)a.st->off[0];
@@ -278,13 +290,17 @@ static int launch_col_pass_e(const ColArgs& a, cudaStream_t s) {
   // once per instantiation and process (plans may run on several host threads)
   static std::once_flag once;
   static cudaError_t cfg_err = cudaSuccess;
+  static int dist = 0;  // CTAs one wave ahead
   std::call_once(once, [] {
     cfg_err = cudaFuncSetAttribute(col_pass_kernel<L, MODE, EV, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)kBytes);
+    if (cfg_err == cudaSuccess) dist = resident_ctas(col_pass_kernel<L, MODE, EV, PREC>, Cfg::THREADS, kBytes);
   });
   if (cfg_err != cudaSuccess) return (int)cfg_err;
   const dim3 grid(ncols / Cfg::W), block(Cfg::THREADS);
-  return launch_pdl(col_pass_kernel<L, MODE, EV, PREC>, grid, block, kBytes, s, a);
+  ColArgs b = a;
+  b.pf = a.prefetch ? dist : 0;
+  return launch_pdl(col_pass_kernel<L, MODE, EV, PREC>, grid, block, kBytes, s, b);
 }
 
 }  // namespace wf

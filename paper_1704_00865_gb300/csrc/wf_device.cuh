@@ -373,6 +373,16 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
 __device__ __forceinline__ void cp_async8(void* dst, const void* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
+// L2 prefetch hint for a contiguous range of bytes (16-byte aligned, a
+// multiple of 16, issued in pieces of at most 64 KB).  It changes no data and
+// no ordering; a later load of the range hits L2.
+__device__ __forceinline__ void prefetch_l2_range(const void* p, size_t bytes) {
+  const char* c = static_cast<const char*>(p);
+  for (size_t o = 0; o < bytes; o += 65536) {
+    const uint32_t n = (uint32_t)(bytes - o < 65536 ? bytes - o : 65536);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(c + o), "r"(n) : "memory");
+  }
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }

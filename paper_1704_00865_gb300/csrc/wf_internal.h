@@ -134,7 +134,23 @@ struct ColArgs {
   float2* warm_copy;          // COL_WARM: tiled copy of the input (t_RF or t_PX)
   int variant;                // column pass shape (0 or 1), chosen by the autotuner
   int prec;                   // radix-16 stages of the column pass: 0 FP32, 1 split TF32, 2 TF32
+  int prefetch;               // column pass: hint the tiles of the CTA one wave ahead into L2
+  int pf;                     // (set by the launcher) that distance in CTAs, 0 = off
 };
+
+// CTAs of a kernel resident at once on the current device (SMs x CTAs per
+// SM for the block and dynamic shared memory), or 0 if the query fails: the
+// distance one wave ahead, for L2 prefetch hints
+template <typename K>
+int resident_ctas(K kernel, int threads, size_t smem) {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return sms * per_sm;
+}
 
 // launchers (return a cudaError_t as int)
 int launch_row(int mode, const RowArgs& a, cudaStream_t s);

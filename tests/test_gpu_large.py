@@ -114,7 +114,7 @@ def test_radix3_sizes_converge_to_closed_form(wf, n):
                     reason="about 10 minutes of FP64 PCG on the host (set WF_LONG_TESTS=1)")
 def test_4096_three_part_masked_solve_against_pcg(wf):
     # the largest map with the benchmark's noise model, mask, solver settings
-    # (up to 8 further corrections while the stop test fails, as the
+    # (further corrections while the stop test fails, as many as the
     # benchmark's 4096^2 leg) and stop test: rel L2 against the FP64 PCG
     # solution (eq. wiener-alt),
     # over all pixels and over the masked pixels alone, and the literal

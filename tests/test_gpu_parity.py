@@ -279,7 +279,7 @@ def test_refined_solve_after_a_stall_passes_the_stop_test(wf):
     assert rel(out.cpu().numpy().astype(np.float64), O.dense_wf(prob)) < 1e-4
 
 
-@pytest.mark.parametrize("shape", [(64, 128), (256, 256), (512, 512), (128, 32), (128, 1024)])
+@pytest.mark.parametrize("shape", [(64, 128), (256, 256), (512, 512), (128, 32), (128, 1024), (4096, 64)])
 def test_both_pass_shapes_match_the_oracle(wf, shape):
     # the autotuner picks one of two compiled shapes per pass; each is held to
     # the same single-sweep parity
