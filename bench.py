@@ -769,9 +769,10 @@ PRECISION_SIZES = (1024, 4096)
 
 def run_precision(args):
     """The radix-16 stages of the column transforms in each arithmetic
-    (dft_precision 0, 1, 2): the benchmark's 1024^2 solve (solves/s, device
-    inputs, L2 flushed between solves) and the per-launch time of the column
-    pass at 1024^2 and 4096^2.  The errors against the FP64 oracle are
+    (dft_precision 0-4): the benchmark's 1024^2 solve (solves/s, device
+    inputs, L2 flushed between solves), the 4096^2 solve of the large leg
+    (where the stages take that column length) and the per-launch time of
+    the passes at 1024^2 and 4096^2.  The errors against the FP64 oracle are
     measured by tests/test_gpu_precision.py."""
     import torch
     from paper_1704_00865_gb300 import build, synth, wf
@@ -802,6 +803,27 @@ def run_precision(args):
         plan.close()
         entry = {"solves_per_s": round(1e3 * len(ms) / sum(ms), 4), "status": st["status"],
                  "sweeps": st["iters"], "final_rel_rho_u": st["rel_rho_u"], "final_rel_rho_m": st["rel_rho_m"]}
+        # the 4096^2 map of the large leg, same solver (one timed solve after a warm-up one)
+        if prec >= 3:
+            entry[f"solve_{LARGE_N}"] = "unsupported: the tcgen05 stages take columns of 512 and 1024"
+        else:
+            lp = synth.make_problem(LARGE_N, LARGE_N, LARGE_SEED)
+            linp = [dev(a) for a in (lp.d, lp.pixel_var, lp.mask, lp.C, lp.P1f, lp.Pst, lp.stripe_amp2)]
+            lout = torch.empty(LARGE_N, LARGE_N, device="cuda")
+            lpl = wf.Plan(LARGE_N, LARGE_N, wf.parts_of(lp),
+                          solver_params(wf, dft_precision=prec, refine_extra=LARGE_REFINE_EXTRA))
+            lpl.solve(*linp, sched, TOL, out=lout)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lst = lpl.solve(*linp, sched, TOL, out=lout)[1]
+            e1.record(stream)
+            e1.synchronize()
+            lpl.close()
+            entry[f"solve_{LARGE_N}"] = {"solves_per_s": round(1e3 / e0.elapsed_time(e1), 4), "status": lst["status"],
+                                         "sweeps": lst["iters"], "final_rel_rho_u": lst["rel_rho_u"],
+                                         "final_rel_rho_m": lst["rel_rho_m"]}
+            del linp, lout
         for n in PRECISION_SIZES:
             if prec >= 3 and n not in TC5_SIZES:
                 continue
