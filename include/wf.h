@@ -53,7 +53,7 @@
 extern "C" {
 #endif
 
-#define WF_ABI_VERSION 2
+#define WF_ABI_VERSION 3
 
 #if defined(__GNUC__)
 #define WF_API __attribute__((visibility("default")))
@@ -131,8 +131,8 @@ typedef struct {
  *                  the iteration then needs no tau for the 1/f part and
  *                  split_f may be 1.  0: the plain sweep.  Default 1.
  *  refine          defect-correction solves wf_solve adds after the first
- *                  (default 0).  Each takes the residual of the accumulated s
- *                  (Sec. 2): Delta d_u = [(I + N S^-1) s - d] on unmasked
+ *                  (default 0, at most 16).  Each takes the residual of the
+ *                  accumulated s (Sec. 2): Delta d_u = [(I + N S^-1) s - d] on unmasked
  *                  pixels and j = (S^-1 s) on masked pixels, solves the same
  *                  filter with Delta d_u as data and j as a source,
  *                  (S^-1 + N^-1) e = N^-1 Delta d + j, and subtracts e =
@@ -162,7 +162,7 @@ typedef struct {
  *  refine_extra    further corrections after the refine ones, each run only
  *                  while the refined s fails the stop test (tol > 0): a
  *                  harder map gets the sweeps it needs without raising the
- *                  budget of every map; default 0, at most 8.
+ *                  budget of every map; default 0, at most 16.
  *  refine_lam1_iters with a cap and a fixed schedule, each correction runs
  *                  the schedule's levels (lambda > 1) for at most
  *                  refine_max_iters - refine_lam1_iters sweeps and then
@@ -209,6 +209,19 @@ typedef struct {
  *                  every checkpoint, not only at lambda = 1); 2 also chi^2_aug
  *                  (wf_chi2_aug) at every checkpoint (merged 2DF block only,
  *                  WF_EUNSUPPORTED otherwise).  Up to 8192 records per problem.
+ *  refine_accel    how the defect corrections are combined: 0 each
+ *                  correction is subtracted (s <- s - e, iterative
+ *                  refinement); m in 1..16 Anderson acceleration with a
+ *                  history of m corrections: with f_k = -e_k the k-th
+ *                  correction of s_k, the next s is s_k + f_k - sum_j
+ *                  gamma_j (Delta s_j + Delta f_j), gamma minimising
+ *                  ||f_k - sum_j gamma_j Delta f_j||_2 over the last m
+ *                  differences of consecutive s and f (the same Krylov space
+ *                  as GMRES on the corrected system, reached without N^-1).
+ *                  The least squares are solved on the host from FP64 dot
+ *                  products taken on the device in a fixed order, so a solve
+ *                  still repeats bit for bit.  Needs refine > 0 to act; the
+ *                  plan keeps 2m + 2 more maps.  Default 0.
  */
 typedef struct {
   double theta[3];
@@ -230,6 +243,7 @@ typedef struct {
   int refine_extra;
   int sweep_kernel;
   int trace;
+  int refine_accel;
 } wf_params;
 
 /* Results of a solve. */

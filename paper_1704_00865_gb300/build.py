@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libwf.so")
 SOURCES = ["wf_rows.cu", "wf_cols.cu", "wf_colpass.cu", "wf_colpass_tc.cu", "wf_ctrl.cu", "wf_api.cu",
-           "wf_static.cu", "wf_batch.cu", "wf_fno.cu", "wf_chi.cu", "wf_fused.cu", "wf_batchk.cu"]
+           "wf_static.cu", "wf_batch.cu", "wf_fno.cu", "wf_chi.cu", "wf_fused.cu", "wf_batchk.cu", "wf_accel.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-I", os.path.join(ROOT, "include")]

@@ -64,6 +64,18 @@ struct wf_plan_s {
   float2* jmap = nullptr;     // source j on masked pixels (pixel pairs)
   float2* src_2df = nullptr;  // its 2D DFT, column-tiled
   bool has_src = false;       // the loaded problem carries the source
+  // Anderson-accelerated corrections (refine_accel = m > 0): the last f,
+  // the last update, m differences of s and of f (ring), their Gram matrix
+  float* aa_fprev = nullptr;
+  float* aa_u = nullptr;
+  float* aa_dx[WF_AA_MAX] = {};
+  float* aa_df[WF_AA_MAX] = {};
+  double* aa_part = nullptr;  // per-block partial dot products
+  double* aa_dot = nullptr;   // their sums (device), then pinned host copy
+  double* h_aa = nullptr;
+  int aa_n = 0, aa_head = 0;  // columns held, oldest column once the ring is full
+  bool aa_have = false;       // aa_fprev holds the previous f
+  double aa_G[WF_AA_MAX][WF_AA_MAX] = {};
   // CUDA graph of one polling chunk of wf_run (K checkpoints of R sweeps),
   // captured and replayed on the plan's own stream (the caller's stream may
   // be the legacy default stream, which cannot be captured)
@@ -85,6 +97,9 @@ struct wf_plan_s {
     long long last_use = 0;
   } chunk[2];
   long long chunk_clock = 0;
+  // an eager chunk has run on this plan, so every kernel's one-time set-up
+  // (attributes, occupancy queries) is done and chunks may be captured
+  bool chunk_warm = false;
   std::vector<void*> allocs;
 };
 
@@ -194,6 +209,7 @@ void wf_plan_destroy(wf_plan_t P) {
   if (P->gstream) cudaStreamDestroy(P->gstream);
   for (void* q : P->allocs) cudaFree(q);
   if (P->h_st) cudaFreeHost(P->h_st);
+  if (P->h_aa) cudaFreeHost(P->h_aa);
   delete P;
 }
 
@@ -228,11 +244,11 @@ int wf::check_plan_args(int ny, int nx, unsigned parts, const wf_params* p) {
       !(prm.split_w >= 0.0 && prm.split_w < 1.0))
     return WF_EINVAL;
   if (!(prm.tol_u_scale > 0.0) || (prm.merge_2df != 0 && prm.merge_2df != 1)) return WF_EINVAL;
-  if (prm.refine < 0 || prm.refine > 8 || !(prm.refine_tol_scale >= 1.0) || prm.refine_max_iters < 0 ||
+  if (prm.refine < 0 || prm.refine > 16 || !(prm.refine_tol_scale >= 1.0) || prm.refine_max_iters < 0 ||
       prm.refine_lam1_iters < 0 || prm.stall_checks < 0 || prm.autotune < 0 || prm.autotune > 2 ||
-      prm.refine_extra < 0 || prm.refine_extra > 8 ||
+      prm.refine_extra < 0 || prm.refine_extra > 16 ||
       prm.dft_precision < 0 || prm.dft_precision > 4 || prm.sweep_kernel < 0 || prm.sweep_kernel > 1 ||
-      prm.trace < 0 || prm.trace > 2)
+      prm.trace < 0 || prm.trace > 2 || prm.refine_accel < 0 || prm.refine_accel > WF_AA_MAX)
     return WF_EINVAL;
   // tensor-core radix-16 stages: 16-value column shapes, merged 2DF block
   if (prm.dft_precision != 0 && (!col_tc_supported(ny) || prm.merge_2df != 1)) return WF_EUNSUPPORTED;
@@ -313,6 +329,16 @@ int wf_plan_create(wf_plan_t* out, int ny, int nx, unsigned parts, const wf_para
     AL(P->rho, npx / 2);
     AL(P->jmap, npx / 2);
     AL(P->src_2df, nh);
+    if (prm.refine_accel > 0) {
+      AL(P->aa_fprev, npx);
+      AL(P->aa_u, npx);
+      for (int j = 0; j < prm.refine_accel; ++j) {
+        AL(P->aa_dx[j], npx);
+        AL(P->aa_df[j], npx);
+      }
+      AL(P->aa_part, (size_t)aa_dots_blocks() * 2 * WF_AA_MAX);
+      AL(P->aa_dot, (size_t)2 * WF_AA_MAX);
+    }
   }
 #undef AL
   if (rc != WF_OK) {
@@ -322,6 +348,12 @@ int wf_plan_create(wf_plan_t* out, int ny, int nx, unsigned parts, const wf_para
   if (cudaMallocHost(&P->h_st, sizeof(WfState)) != cudaSuccess) {
     cudaGetLastError();
     P->h_st = nullptr;
+    wf_plan_destroy(P);
+    return WF_ENOMEM;
+  }
+  if (P->aa_dot && cudaMallocHost(&P->h_aa, 2 * WF_AA_MAX * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    P->h_aa = nullptr;
     wf_plan_destroy(P);
     return WF_ENOMEM;
   }
@@ -1051,7 +1083,9 @@ static int wf_run_on(wf_plan_t P, const wf_schedule* sch, double tol, wf_stats* 
   P->launches += 1;
   const long long it0 = P->it_done;
   long long enq = it0;
-  const int K = P->p.check_every;
+  // checkpoints per chunk: check_every, or fewer when the run's cap ends
+  // sooner (a short correction solve is then one captured chunk)
+  const int K = (int)std::max<long long>(1, std::min<long long>(P->p.check_every, ((long long)c.max_iters + R - 1) / R));
   const long long cap = it0 + (long long)c.max_iters;
   const long long per_chunk = (long long)K * R;
   // one chunk: K checkpoints, each R sweeps then the residual and the controller
@@ -1089,10 +1123,9 @@ static int wf_run_on(wf_plan_t P, const wf_schedule* sch, double tol, wf_stats* 
   put(&par, 8); put(&src, 8);
   if (P->p.trace) put(&c.run_index, 4);  // stamped into trace records
   const bool use_graph = (per_chunk % 2 == 0);
-  bool first = true;
   for (;;) {
     const bool full = enq + per_chunk <= cap;
-    if (use_graph && full && !first) {
+    if (use_graph && full && P->chunk_warm) {
       wf_plan_s::ChunkGraph* G = nullptr;
       for (auto& g : P->chunk)
         if (g.exec && g.key == key) G = &g;
@@ -1129,8 +1162,8 @@ static int wf_run_on(wf_plan_t P, const wf_schedule* sch, double tol, wf_stats* 
       int rc = enqueue_chunk(enq);
       if (rc) return rc;
       enq = std::min(cap, e0 + per_chunk);
+      P->chunk_warm = true;
     }
-    first = false;
     CK(cudaMemcpyAsync(P->h_st, P->st, sizeof(WfState), cudaMemcpyDeviceToHost, P->stream));
     CK(cudaStreamSynchronize(P->stream));
     if (P->h_st->done || enq >= cap) break;
@@ -1305,6 +1338,8 @@ int wf::job_after_first(SolveJob& J, int run_status, const wf_stats& s0, bool* d
   int rc = wf_get_field(P, WF_FIELD_S, P->s_acc);
   if (rc) return rc;
   J.tot = s0;
+  P->aa_n = P->aa_head = 0;
+  P->aa_have = false;
   // a source on masked pixels needs the merged 2DF block (or no 1/f part)
   J.with_src = !(P->has_f && !P->merge);
   // A capped correction runs the fixed schedule's levels for at most
@@ -1333,6 +1368,100 @@ int wf::job_after_first(SolveJob& J, int run_status, const wf_stats& s0, bool* d
     J.csched.nlevels = (int)J.clam.size();
   }
   *done = false;
+  return WF_OK;
+}
+
+// Solve (G + eps diag) g = b for the m x m Gram matrix G by Cholesky in
+// FP64; a column whose pivot falls below 1e-10 of the largest diagonal
+// (linearly dependent on the others, to FP32 accuracy) gets gamma = 0.
+static void aa_solve(int m, const double G[WF_AA_MAX][WF_AA_MAX], const double* b, double* g) {
+  double L[WF_AA_MAX][WF_AA_MAX] = {};
+  bool use[WF_AA_MAX];
+  double dmax = 0.0;
+  for (int i = 0; i < m; ++i) dmax = std::max(dmax, G[i][i]);
+  for (int i = 0; i < m; ++i) {
+    use[i] = false;
+    g[i] = 0.0;
+    if (!(dmax > 0.0)) continue;
+    double d = G[i][i] * (1.0 + 1e-12);
+    for (int k = 0; k < i; ++k)
+      if (use[k]) d -= L[i][k] * L[i][k];
+    if (!(d > 1e-10 * dmax)) continue;
+    use[i] = true;
+    L[i][i] = sqrt(d);
+    for (int r = i + 1; r < m; ++r) {
+      double v = G[r][i];
+      for (int k = 0; k < i; ++k)
+        if (use[k]) v -= L[r][k] * L[i][k];
+      L[r][i] = v / L[i][i];
+    }
+  }
+  double y[WF_AA_MAX] = {};
+  for (int i = 0; i < m; ++i) {
+    if (!use[i]) continue;
+    double v = b[i];
+    for (int k = 0; k < i; ++k)
+      if (use[k]) v -= L[i][k] * y[k];
+    y[i] = v / L[i][i];
+  }
+  for (int i = m - 1; i >= 0; --i) {
+    if (!use[i]) continue;
+    double v = y[i];
+    for (int k = i + 1; k < m; ++k)
+      if (use[k]) v -= L[k][i] * g[k];
+    g[i] = v / L[i][i];
+  }
+}
+
+// Anderson step for the correction e = s_corr of x = s_acc (refine_accel):
+// f = -e; the newest differences Delta f = f - f_prev and Delta x (the
+// previous update) enter the ring; gamma minimises ||f - Delta F gamma||_2;
+// x += f - (Delta X + Delta F) gamma.  The first correction is the plain one.
+static int anderson_step(wf_plan_s* P) {
+  const size_t npx = (size_t)P->ny * P->nx;
+  const int m = P->p.refine_accel;
+  int slot = -1;
+  if (P->aa_have) {
+    slot = P->aa_n < m ? P->aa_n : P->aa_head;
+    std::swap(P->aa_dx[slot], P->aa_u);  // Delta x of the new column: the previous update
+  }
+  CKI(launch_aa_diff(slot >= 0 ? P->aa_df[slot] : nullptr, P->aa_fprev, P->s_corr, npx, P->stream));
+  P->launches += 1;
+  if (slot >= 0) {
+    if (P->aa_n < m) P->aa_n += 1;
+    else P->aa_head = (P->aa_head + 1) % m;
+  }
+  P->aa_have = true;
+  const int n = P->aa_n;
+  double gamma[WF_AA_MAX] = {};
+  if (n > 0) {
+    // Delta f_new . Delta f_j and f . Delta f_j for every held column
+    AADots d{};
+    d.a0 = P->aa_df[slot];
+    d.a1 = P->aa_fprev;
+    for (int j = 0; j < n; ++j) d.b[j] = P->aa_df[j];
+    d.nb = n;
+    CKI(launch_aa_dots(d, npx, P->aa_part, P->aa_dot, P->stream));
+    P->launches += 2;
+    CK(cudaMemcpyAsync(P->h_aa, P->aa_dot, 2 * WF_AA_MAX * sizeof(double), cudaMemcpyDeviceToHost, P->stream));
+    CK(cudaStreamSynchronize(P->stream));
+    for (int j = 0; j < n; ++j) P->aa_G[slot][j] = P->aa_G[j][slot] = P->h_aa[j];
+    double b[WF_AA_MAX];
+    for (int j = 0; j < n; ++j) b[j] = P->h_aa[WF_AA_MAX + j];
+    aa_solve(n, P->aa_G, b, gamma);
+  }
+  AAUpdate u{};
+  u.x = P->s_acc;
+  u.u = P->aa_u;
+  u.f = P->aa_fprev;
+  for (int j = 0; j < n; ++j) {
+    u.dx[j] = P->aa_dx[j];
+    u.df[j] = P->aa_df[j];
+    u.gamma[j] = (float)gamma[j];
+  }
+  u.nj = n;
+  CKI(launch_aa_update(u, npx, P->stream));
+  P->launches += 1;
   return WF_OK;
 }
 
@@ -1386,8 +1515,12 @@ int wf::job_corr_end(SolveJob& J, int run_status, const wf_stats& sr) {
   if (run_status != WF_OK && P->p.refine_max_iters == 0 && J.status == WF_OK) J.status = run_status;
   J.tot.iters += sr.iters;
   J.tot.checkpoints += sr.checkpoints;
-  CKI(launch_sub(P->s_acc, P->s_corr, npx, P->stream));
-  P->launches += 1;
+  if (P->p.refine_accel > 0) {
+    if ((rc = anderson_step(P))) return rc;
+  } else {
+    CKI(launch_sub(P->s_acc, P->s_corr, npx, P->stream));
+    P->launches += 1;
+  }
   J.corrections += 1;
   return WF_OK;
 }

@@ -341,6 +341,29 @@ int launch_set_lambda(WfState* st, double lam, int reset, cudaStream_t s);
 int launch_pack_data(float4* dn_out, const float4* dn_in, const float2* rho, size_t npair,
                      double* part, WfState* st, cudaStream_t s);
 int launch_sub(float* y, const float* x, size_t n, cudaStream_t s);
+
+// Anderson-accelerated defect correction (wf_accel.cu): history of at most
+// WF_AA_MAX corrections
+constexpr int WF_AA_MAX = 16;
+struct AADots {               // a0 . b_j and a1 . b_j, j < nb
+  const float* a0;
+  const float* a1;
+  const float* b[WF_AA_MAX];
+  int nb;
+};
+struct AAUpdate {             // u = f - sum_j gamma_j (dx_j + df_j); x += u
+  float* x;
+  float* u;
+  const float* f;
+  const float* dx[WF_AA_MAX];
+  const float* df[WF_AA_MAX];
+  float gamma[WF_AA_MAX];
+  int nj;
+};
+int aa_dots_blocks();         // partial sums per dot product (upper bound)
+int launch_aa_diff(float* df, float* fprev, const float* e, size_t n, cudaStream_t s);
+int launch_aa_dots(const AADots& a, size_t n, double* part, double* out, cudaStream_t s);
+int launch_aa_update(const AAUpdate& a, size_t n, cudaStream_t s);
 // y[i] = v;  y[i] = a x[i]
 int launch_fill(float* y, float v, size_t n, cudaStream_t s);
 

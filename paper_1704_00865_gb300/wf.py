@@ -46,7 +46,7 @@ class wf_params(C.Structure):
                 ("refine_tol_scale", C.c_double), ("refine_max_iters", C.c_int),
                 ("refine_lam1_iters", C.c_int), ("stall_checks", C.c_int), ("autotune", C.c_int),
                 ("dft_precision", C.c_int), ("refine_extra", C.c_int), ("sweep_kernel", C.c_int),
-                ("trace", C.c_int)]
+                ("trace", C.c_int), ("refine_accel", C.c_int)]
 
 
 class wf_stats(C.Structure):
@@ -185,10 +185,13 @@ def make_params(theta=None, split_f=None, split_w=None, residual_every=None, max
                 check_every=None, merge_2df=None, tol_u_scale=None, split_fp=None,
                 refine=None, refine_tol_scale=None, refine_max_iters=None,
                 refine_lam1_iters=None, stall_checks=None, autotune=None,
-                dft_precision=None, refine_extra=None, sweep_kernel=None, trace=None) -> wf_params:
+                dft_precision=None, refine_extra=None, sweep_kernel=None, trace=None,
+                refine_accel=None) -> wf_params:
     p = wf_params_default()
     if trace is not None:
         p.trace = int(trace)
+    if refine_accel is not None:
+        p.refine_accel = int(refine_accel)
     if sweep_kernel is not None:
         p.sweep_kernel = int(sweep_kernel)
     if refine_extra is not None:
