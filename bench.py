@@ -52,17 +52,19 @@ SCHED_LEVELS_ITERS = [1000, 2000, 2000, 2000]
 # of the first level), followed by REFINE defect-correction solves of
 # REFINE_MAX_ITERS sweeps each (residual of the accumulated s: unmasked data
 # and masked-pixel source; each runs the cooling levels for
-# REFINE_MAX_ITERS - REFINE_LAM1_ITERS sweeps, then lambda = 1).  Slow modes
+# REFINE_MAX_ITERS - REFINE_LAM1_ITERS sweeps, then lambda = 1), combined by
+# Anderson acceleration over the last REFINE_ACCEL corrections.  Slow modes
 # (low-k_x stripe modes, masked discs) are what the corrections remove; the
 # refined s is judged by the stop test itself.  The budget was chosen on
 # seeds 1000-1003 against the FP64 PCG solution, with the error over the
 # masked pixels alone as the binding bound (it runs about six times the
-# whole-map error): 8300 sweeps, whole-map rel L2 <= 8.8e-6, masked pixels
-# <= 5.1e-5.  Each 1000-sweep correction divides the error by about 2.3.
+# whole-map error): 3500 sweeps, whole-map rel L2 <= 6.4e-6, masked pixels
+# <= 3.7e-5 (plain corrections needed 8300 sweeps for 8.8e-6 and 5.1e-5).
 FIRST_SOLVE_SWEEPS = 300
-REFINE = 8
-REFINE_MAX_ITERS = 1000
-REFINE_LAM1_ITERS = 300
+REFINE = 16
+REFINE_MAX_ITERS = 200
+REFINE_LAM1_ITERS = 50
+REFINE_ACCEL = 8
 # up to this many further corrections, each only while the refined s still
 # fails the stop test (amplitude-jittered 2048^2 maps of the batch workload
 # may need them on the masked-pixel criterion; the 1024^2 map none)
@@ -89,7 +91,7 @@ def solver_params(wf, **override):
               merge_2df=1, split_f=SPLIT_F, split_fp=SPLIT_FP, tol_u_scale=TOL_U_SCALE,
               refine=REFINE, refine_max_iters=REFINE_MAX_ITERS,
               refine_lam1_iters=REFINE_LAM1_ITERS, refine_tol_scale=1.0, stall_checks=STALL_CHECKS,
-              refine_extra=REFINE_EXTRA)
+              refine_extra=REFINE_EXTRA, refine_accel=REFINE_ACCEL)
     kw.update(override)
     return wf.make_params(**kw)
 
@@ -116,7 +118,7 @@ def workload_config():
                      "literal_residual_target": 1e-5, "rel_error_target": 1e-4},
             "first_solve_max_sweeps": FIRST_SOLVE_SWEEPS,
             "refine": {"solves": REFINE, "sweeps_each": REFINE_MAX_ITERS,
-                       "of_which_at_lambda_1": REFINE_LAM1_ITERS,
+                       "of_which_at_lambda_1": REFINE_LAM1_ITERS, "anderson_history": REFINE_ACCEL,
                        "more_while_stop_test_fails": REFINE_EXTRA},
             "params": {"merge_2df": 1, "split_f": SPLIT_F, "split_fp": SPLIT_FP, "theta": [0.9, 0.9, 1.0],
                        "stall_checks": STALL_CHECKS},
@@ -287,7 +289,7 @@ def run_reference(args):
 LARGE_N = 4096
 LARGE_SEED = 3000
 # further corrections the 4096^2 map may take while it fails the stop test
-LARGE_REFINE_EXTRA = 8
+LARGE_REFINE_EXTRA = 16
 
 
 def large_leg(wf, torch, peak):
@@ -619,7 +621,7 @@ WARM_FNO = dict(width=32, mx=16, my=16, layers=4)
 # With the headline's short first solve and four corrections it saves
 # nothing: from zero, the same budgets reach the same accuracy.
 WARM_LAM, WARM_ITERS = [30.0, 10.0, 3.0, 1.5], [500, 1000, 1000, 1000]
-LONG_FIRST_SOLVE = dict(max_iters=60000, refine=1, refine_max_iters=4000)
+LONG_FIRST_SOLVE = dict(max_iters=60000, refine=1, refine_max_iters=4000, refine_lam1_iters=300)
 
 
 def warm_schedule(wf):
