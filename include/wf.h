@@ -218,9 +218,9 @@ typedef struct {
  *                  ||f_k - sum_j gamma_j Delta f_j||_2 over the last m
  *                  differences of consecutive s and f (the same Krylov space
  *                  as GMRES on the corrected system, reached without N^-1).
- *                  The least squares are solved on the host from FP64 dot
- *                  products taken on the device in a fixed order, so a solve
- *                  still repeats bit for bit.  Needs refine > 0 to act; the
+ *                  The FP64 dot products (summed in a fixed order) and the
+ *                  least squares run on the device, so a solve still repeats
+ *                  bit for bit and a correction needs no host round trip.  Needs refine > 0 to act; the
  *                  plan keeps 2m + 2 more maps.  Default 0.
  */
 typedef struct {

@@ -1,7 +1,8 @@
 // wf_accel.cu -- the device side of the Anderson-accelerated defect
 // correction (wf_params.refine_accel): with x = s and f = -e the correction
 // a solve returns for x, keep the differences of consecutive f and x, take
-// the FP64 dot products the least-squares step needs, and form the update.
+// the FP64 dot products, solve the small least-squares problem, and form
+// the update -- all on the device, so a correction needs no host round trip.
 // Every map is a flat array of n floats (n a multiple of 4, 16-byte aligned).
 #include <cuda_runtime.h>
 
@@ -66,13 +67,60 @@ __global__ void __launch_bounds__(kThreads) aa_dots_kernel(AADots a, size_t n4, 
   }
 }
 
-// the partials of all blocks, summed in block order
-__global__ void aa_reduce_kernel(const double* part, int nblocks, double* out) {
+// The partials of all blocks summed in block order (thread j: dot j), then,
+// by one thread, the least-squares step: row and column `slot` of the Gram
+// matrix G = Delta F^T Delta F (held in device memory across corrections)
+// take the new products, and (G + eps diag) gamma = Delta F^T f is solved by
+// Cholesky in FP64.  A column whose pivot falls below 1e-10 of the largest
+// diagonal (dependent on the others to FP32 accuracy) gets gamma = 0.
+__global__ void aa_solve_kernel(const double* part, int nblocks, int slot, int n, double* G, float* gamma) {
+  __shared__ double dots[2 * WF_AA_MAX];
   const int j = threadIdx.x;
-  if (j >= 2 * WF_AA_MAX) return;
-  double v = 0.0;
-  for (int b = 0; b < nblocks; ++b) v += part[(size_t)b * 2 * WF_AA_MAX + j];
-  out[j] = v;
+  if (j < 2 * WF_AA_MAX) {
+    double v = 0.0;
+    for (int b = 0; b < nblocks; ++b) v += part[(size_t)b * 2 * WF_AA_MAX + j];
+    dots[j] = v;
+  }
+  __syncthreads();
+  if (j != 0) return;
+  for (int k = 0; k < n; ++k) G[slot * WF_AA_MAX + k] = G[k * WF_AA_MAX + slot] = dots[k];
+  double L[WF_AA_MAX][WF_AA_MAX];
+  bool use[WF_AA_MAX];
+  double g[WF_AA_MAX], y[WF_AA_MAX];
+  double dmax = 0.0;
+  for (int i = 0; i < n; ++i) dmax = fmax(dmax, G[i * WF_AA_MAX + i]);
+  for (int i = 0; i < n; ++i) {
+    use[i] = false;
+    g[i] = y[i] = 0.0;
+    if (!(dmax > 0.0)) continue;
+    double d = G[i * WF_AA_MAX + i] * (1.0 + 1e-12);
+    for (int k = 0; k < i; ++k)
+      if (use[k]) d -= L[i][k] * L[i][k];
+    if (!(d > 1e-10 * dmax)) continue;
+    use[i] = true;
+    L[i][i] = sqrt(d);
+    for (int r = i + 1; r < n; ++r) {
+      double v = G[r * WF_AA_MAX + i];
+      for (int k = 0; k < i; ++k)
+        if (use[k]) v -= L[r][k] * L[i][k];
+      L[r][i] = v / L[i][i];
+    }
+  }
+  for (int i = 0; i < n; ++i) {
+    if (!use[i]) continue;
+    double v = dots[WF_AA_MAX + i];
+    for (int k = 0; k < i; ++k)
+      if (use[k]) v -= L[i][k] * y[k];
+    y[i] = v / L[i][i];
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    if (!use[i]) continue;
+    double v = y[i];
+    for (int k = i + 1; k < n; ++k)
+      if (use[k]) v -= L[k][i] * g[k];
+    g[i] = v / L[i][i];
+  }
+  for (int i = 0; i < WF_AA_MAX; ++i) gamma[i] = i < n ? (float)g[i] : 0.f;
 }
 
 // u = f - sum_j gamma_j (dx_j + df_j); x += u
@@ -85,7 +133,7 @@ __global__ void aa_update_kernel(AAUpdate a, size_t n4) {
     for (int j = 0; j < a.nj; ++j) {
       const float4 p = reinterpret_cast<const float4*>(a.dx[j])[i];
       const float4 q = reinterpret_cast<const float4*>(a.df[j])[i];
-      const float g = a.gamma[j];
+      const float g = __ldg(&a.gamma[j]);
       v.x -= g * (p.x + q.x);
       v.y -= g * (p.y + q.y);
       v.z -= g * (p.z + q.z);
@@ -118,13 +166,13 @@ int launch_aa_diff(float* df, float* fprev, const float* e, size_t n, cudaStream
   return (int)cudaGetLastError();
 }
 
-int launch_aa_dots(const AADots& a, size_t n, double* part, double* out, cudaStream_t s) {
+int launch_aa_lsq(const AADots& a, size_t n, double* part, int slot, double* G, float* gamma, cudaStream_t s) {
   const size_t n4 = n / 4;
   const int g = std::min(grid_for(n4), aa_dots_blocks());
   aa_dots_kernel<<<g, kThreads, 0, s>>>(a, n4, part);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return (int)e;
-  aa_reduce_kernel<<<1, 2 * WF_AA_MAX, 0, s>>>(part, g, out);
+  aa_solve_kernel<<<1, 2 * WF_AA_MAX, 0, s>>>(part, g, slot, a.nb, G, gamma);
   return (int)cudaGetLastError();
 }
 

@@ -71,11 +71,10 @@ struct wf_plan_s {
   float* aa_dx[WF_AA_MAX] = {};
   float* aa_df[WF_AA_MAX] = {};
   double* aa_part = nullptr;  // per-block partial dot products
-  double* aa_dot = nullptr;   // their sums (device), then pinned host copy
-  double* h_aa = nullptr;
+  double* aa_G = nullptr;     // Gram matrix of the held Delta f (device)
+  float* aa_gamma = nullptr;  // least-squares coefficients (device)
   int aa_n = 0, aa_head = 0;  // columns held, oldest column once the ring is full
   bool aa_have = false;       // aa_fprev holds the previous f
-  double aa_G[WF_AA_MAX][WF_AA_MAX] = {};
   // CUDA graph of one polling chunk of wf_run (K checkpoints of R sweeps),
   // captured and replayed on the plan's own stream (the caller's stream may
   // be the legacy default stream, which cannot be captured)
@@ -209,7 +208,6 @@ void wf_plan_destroy(wf_plan_t P) {
   if (P->gstream) cudaStreamDestroy(P->gstream);
   for (void* q : P->allocs) cudaFree(q);
   if (P->h_st) cudaFreeHost(P->h_st);
-  if (P->h_aa) cudaFreeHost(P->h_aa);
   delete P;
 }
 
@@ -337,7 +335,8 @@ int wf_plan_create(wf_plan_t* out, int ny, int nx, unsigned parts, const wf_para
         AL(P->aa_df[j], npx);
       }
       AL(P->aa_part, (size_t)aa_dots_blocks() * 2 * WF_AA_MAX);
-      AL(P->aa_dot, (size_t)2 * WF_AA_MAX);
+      AL(P->aa_G, (size_t)WF_AA_MAX * WF_AA_MAX);
+      AL(P->aa_gamma, (size_t)WF_AA_MAX);
     }
   }
 #undef AL
@@ -348,12 +347,6 @@ int wf_plan_create(wf_plan_t* out, int ny, int nx, unsigned parts, const wf_para
   if (cudaMallocHost(&P->h_st, sizeof(WfState)) != cudaSuccess) {
     cudaGetLastError();
     P->h_st = nullptr;
-    wf_plan_destroy(P);
-    return WF_ENOMEM;
-  }
-  if (P->aa_dot && cudaMallocHost(&P->h_aa, 2 * WF_AA_MAX * sizeof(double)) != cudaSuccess) {
-    cudaGetLastError();
-    P->h_aa = nullptr;
     wf_plan_destroy(P);
     return WF_ENOMEM;
   }
@@ -1371,52 +1364,12 @@ int wf::job_after_first(SolveJob& J, int run_status, const wf_stats& s0, bool* d
   return WF_OK;
 }
 
-// Solve (G + eps diag) g = b for the m x m Gram matrix G by Cholesky in
-// FP64; a column whose pivot falls below 1e-10 of the largest diagonal
-// (linearly dependent on the others, to FP32 accuracy) gets gamma = 0.
-static void aa_solve(int m, const double G[WF_AA_MAX][WF_AA_MAX], const double* b, double* g) {
-  double L[WF_AA_MAX][WF_AA_MAX] = {};
-  bool use[WF_AA_MAX];
-  double dmax = 0.0;
-  for (int i = 0; i < m; ++i) dmax = std::max(dmax, G[i][i]);
-  for (int i = 0; i < m; ++i) {
-    use[i] = false;
-    g[i] = 0.0;
-    if (!(dmax > 0.0)) continue;
-    double d = G[i][i] * (1.0 + 1e-12);
-    for (int k = 0; k < i; ++k)
-      if (use[k]) d -= L[i][k] * L[i][k];
-    if (!(d > 1e-10 * dmax)) continue;
-    use[i] = true;
-    L[i][i] = sqrt(d);
-    for (int r = i + 1; r < m; ++r) {
-      double v = G[r][i];
-      for (int k = 0; k < i; ++k)
-        if (use[k]) v -= L[r][k] * L[i][k];
-      L[r][i] = v / L[i][i];
-    }
-  }
-  double y[WF_AA_MAX] = {};
-  for (int i = 0; i < m; ++i) {
-    if (!use[i]) continue;
-    double v = b[i];
-    for (int k = 0; k < i; ++k)
-      if (use[k]) v -= L[i][k] * y[k];
-    y[i] = v / L[i][i];
-  }
-  for (int i = m - 1; i >= 0; --i) {
-    if (!use[i]) continue;
-    double v = y[i];
-    for (int k = i + 1; k < m; ++k)
-      if (use[k]) v -= L[k][i] * g[k];
-    g[i] = v / L[i][i];
-  }
-}
-
 // Anderson step for the correction e = s_corr of x = s_acc (refine_accel):
 // f = -e; the newest differences Delta f = f - f_prev and Delta x (the
 // previous update) enter the ring; gamma minimises ||f - Delta F gamma||_2;
 // x += f - (Delta X + Delta F) gamma.  The first correction is the plain one.
+// Only launches: the ring's bookkeeping is on the host, the arithmetic
+// (including the least squares) on the device.
 static int anderson_step(wf_plan_s* P) {
   const size_t npx = (size_t)P->ny * P->nx;
   const int m = P->p.refine_accel;
@@ -1433,22 +1386,16 @@ static int anderson_step(wf_plan_s* P) {
   }
   P->aa_have = true;
   const int n = P->aa_n;
-  double gamma[WF_AA_MAX] = {};
   if (n > 0) {
-    // Delta f_new . Delta f_j and f . Delta f_j for every held column
+    // Delta f_new . Delta f_j and f . Delta f_j for every held column, the
+    // Gram matrix's new row and the least-squares gamma, on the device
     AADots d{};
     d.a0 = P->aa_df[slot];
     d.a1 = P->aa_fprev;
     for (int j = 0; j < n; ++j) d.b[j] = P->aa_df[j];
     d.nb = n;
-    CKI(launch_aa_dots(d, npx, P->aa_part, P->aa_dot, P->stream));
+    CKI(launch_aa_lsq(d, npx, P->aa_part, slot, P->aa_G, P->aa_gamma, P->stream));
     P->launches += 2;
-    CK(cudaMemcpyAsync(P->h_aa, P->aa_dot, 2 * WF_AA_MAX * sizeof(double), cudaMemcpyDeviceToHost, P->stream));
-    CK(cudaStreamSynchronize(P->stream));
-    for (int j = 0; j < n; ++j) P->aa_G[slot][j] = P->aa_G[j][slot] = P->h_aa[j];
-    double b[WF_AA_MAX];
-    for (int j = 0; j < n; ++j) b[j] = P->h_aa[WF_AA_MAX + j];
-    aa_solve(n, P->aa_G, b, gamma);
   }
   AAUpdate u{};
   u.x = P->s_acc;
@@ -1457,11 +1404,24 @@ static int anderson_step(wf_plan_s* P) {
   for (int j = 0; j < n; ++j) {
     u.dx[j] = P->aa_dx[j];
     u.df[j] = P->aa_df[j];
-    u.gamma[j] = (float)gamma[j];
   }
+  u.gamma = P->aa_gamma;
   u.nj = n;
   CKI(launch_aa_update(u, npx, P->stream));
   P->launches += 1;
+  return WF_OK;
+}
+
+// s of the loaded problem's current state into the device map dst (the
+// kernels of wf_get_field's WF_FIELD_S, without its host wait)
+static int enqueue_s_field(wf_plan_s* P, float* dst) {
+  ColArgs ca = col_args(P, (int)(P->it_done & 1));
+  CKI(launch_col(COL_RESID_A, ca, P->stream));
+  RowArgs ra = row_args(P);
+  ra.out_px = (float2*)dst;
+  ra.in_rf = P->r_q;
+  CKI(launch_row(ROW_C2R, ra, P->stream));
+  P->launches += 2;
   return WF_OK;
 }
 
@@ -1507,7 +1467,7 @@ int wf::job_corr_end(SolveJob& J, int run_status, const wf_stats& sr) {
   const size_t npx = (size_t)P->ny * P->nx;
   P->p.max_iters = J.main_cap;
   int rc = WF_OK;
-  if (finished_rc(run_status)) rc = wf_get_field(P, WF_FIELD_S, P->s_corr);
+  if (finished_rc(run_status)) rc = enqueue_s_field(P, P->s_corr);
   P->has_src = false;
   if (!finished_rc(run_status)) return run_status;
   if (rc) return rc;

@@ -357,12 +357,15 @@ struct AAUpdate {             // u = f - sum_j gamma_j (dx_j + df_j); x += u
   const float* f;
   const float* dx[WF_AA_MAX];
   const float* df[WF_AA_MAX];
-  float gamma[WF_AA_MAX];
+  const float* gamma;         // device, WF_AA_MAX values
   int nj;
 };
 int aa_dots_blocks();         // partial sums per dot product (upper bound)
 int launch_aa_diff(float* df, float* fprev, const float* e, size_t n, cudaStream_t s);
-int launch_aa_dots(const AADots& a, size_t n, double* part, double* out, cudaStream_t s);
+// the dot products a0 . b_j, a1 . b_j, then row and column `slot` of the Gram
+// matrix G (WF_AA_MAX x WF_AA_MAX doubles) and gamma (WF_AA_MAX floats) of
+// (G + eps diag) gamma = (a1 . b_j), all in device memory
+int launch_aa_lsq(const AADots& a, size_t n, double* part, int slot, double* G, float* gamma, cudaStream_t s);
 int launch_aa_update(const AAUpdate& a, size_t n, cudaStream_t s);
 // y[i] = v;  y[i] = a x[i]
 int launch_fill(float* y, float v, size_t n, cudaStream_t s);
