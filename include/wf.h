@@ -131,7 +131,7 @@ typedef struct {
  *                  the iteration then needs no tau for the 1/f part and
  *                  split_f may be 1.  0: the plain sweep.  Default 1.
  *  refine          defect-correction solves wf_solve adds after the first
- *                  (default 0, at most 16).  Each takes the residual of the
+ *                  (default 0, at most 32).  Each takes the residual of the
  *                  accumulated s (Sec. 2): Delta d_u = [(I + N S^-1) s - d] on unmasked
  *                  pixels and j = (S^-1 s) on masked pixels, solves the same
  *                  filter with Delta d_u as data and j as a source,
@@ -162,7 +162,7 @@ typedef struct {
  *  refine_extra    further corrections after the refine ones, each run only
  *                  while the refined s fails the stop test (tol > 0): a
  *                  harder map gets the sweeps it needs without raising the
- *                  budget of every map; default 0, at most 16.
+ *                  budget of every map; default 0, at most 32.
  *  refine_lam1_iters with a cap and a fixed schedule, each correction runs
  *                  the schedule's levels (lambda > 1) for at most
  *                  refine_max_iters - refine_lam1_iters sweeps and then

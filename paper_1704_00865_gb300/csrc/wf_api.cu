@@ -242,9 +242,9 @@ int wf::check_plan_args(int ny, int nx, unsigned parts, const wf_params* p) {
       !(prm.split_w >= 0.0 && prm.split_w < 1.0))
     return WF_EINVAL;
   if (!(prm.tol_u_scale > 0.0) || (prm.merge_2df != 0 && prm.merge_2df != 1)) return WF_EINVAL;
-  if (prm.refine < 0 || prm.refine > 16 || !(prm.refine_tol_scale >= 1.0) || prm.refine_max_iters < 0 ||
+  if (prm.refine < 0 || prm.refine > 32 || !(prm.refine_tol_scale >= 1.0) || prm.refine_max_iters < 0 ||
       prm.refine_lam1_iters < 0 || prm.stall_checks < 0 || prm.autotune < 0 || prm.autotune > 2 ||
-      prm.refine_extra < 0 || prm.refine_extra > 16 ||
+      prm.refine_extra < 0 || prm.refine_extra > 32 ||
       prm.dft_precision < 0 || prm.dft_precision > 4 || prm.sweep_kernel < 0 || prm.sweep_kernel > 1 ||
       prm.trace < 0 || prm.trace > 2 || prm.refine_accel < 0 || prm.refine_accel > WF_AA_MAX)
     return WF_EINVAL;

@@ -71,10 +71,10 @@ def test_plan_create_rejects_bad_arguments_before_any_cuda_call(lib, ny, nx, par
 def test_plan_create_rejects_bad_params(lib):
     from paper_1704_00865_gb300 import wf
     for kw in (dict(theta=(0.9, 1.5, 1.0)), dict(split_f=0.5, split_fp=0.5, merge_2df=0), dict(split_f=1.01, split_fp=0.0), dict(split_f=0.6, split_fp=0.6),
-               dict(residual_every=0), dict(tol_u_scale=0.0), dict(refine=-1), dict(refine=17),
+               dict(residual_every=0), dict(tol_u_scale=0.0), dict(refine=-1), dict(refine=33),
                dict(refine_max_iters=-1), dict(refine_lam1_iters=-1), dict(stall_checks=-1),
                dict(autotune=3), dict(dft_precision=-1), dict(dft_precision=5), dict(sweep_kernel=2), dict(trace=3), dict(refine_accel=-1), dict(refine_accel=17),
-               dict(refine_extra=-1), dict(refine_extra=17)):
+               dict(refine_extra=-1), dict(refine_extra=33)):
         p = wf.make_params(**kw)
         h = C.c_void_p()
         assert lib.wf_plan_create(C.byref(h), 64, 64, 7, C.byref(p), None) == wf.WF_EINVAL
@@ -156,7 +156,7 @@ def test_batch_create_rejects_bad_arguments_before_any_cuda_call(lib, sizes, lan
     p = wf.wf_params_default()
     assert lib.wf_batch_create(C.byref(h), n, ny, nx, parts, C.byref(p), lanes, None) == code
     assert h.value is None
-    bad = wf.make_params(refine=17)
+    bad = wf.make_params(refine=33)
     if n:
         assert lib.wf_batch_create(C.byref(h), n, ny, nx, 7, C.byref(bad), 1, None) in (wf.WF_EINVAL, code)
 
