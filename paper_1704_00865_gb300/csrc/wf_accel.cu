@@ -28,16 +28,20 @@ __global__ void aa_diff_kernel(float4* df, float4* fprev, const float4* e, size_
   }
 }
 
-__device__ __forceinline__ double dot4(const float4 a, const float4 b) {
-  return (double)a.x * b.x + (double)a.y * b.y + (double)a.z * b.z + (double)a.w * b.w;
+__device__ __forceinline__ float dot4(const float4 a, const float4 b) {
+  return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
 }
 
-// per-block partial sums of a0 . b_j and a1 . b_j (j < nb), FP64, in a fixed
-// order: each thread its grid-stride share, then the block's warps
+// Per-block partial sums of a0 . b_j and a1 . b_j (j < nb) in a fixed order:
+// each thread its grid-stride share in FP32 (a few float4 per thread), the
+// warp's 32 lanes in FP32 by a shuffle tree, then the block's warps in FP64.
+// The FP64 units of this GPU are few, so FP64 is kept to the sums of
+// partials (about 2.5e-7 relative error per warp sum of a few hundred
+// products, below the FP32 maps' own precision).
 __global__ void __launch_bounds__(kThreads) aa_dots_kernel(AADots a, size_t n4, double* part) {
-  double acc[2 * WF_AA_MAX];
+  float acc[2 * WF_AA_MAX];
 #pragma unroll
-  for (int j = 0; j < 2 * WF_AA_MAX; ++j) acc[j] = 0.0;
+  for (int j = 0; j < 2 * WF_AA_MAX; ++j) acc[j] = 0.f;
   const float4* a0 = reinterpret_cast<const float4*>(a.a0);
   const float4* a1 = reinterpret_cast<const float4*>(a.a1);
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n4; i += (size_t)gridDim.x * blockDim.x) {
@@ -55,9 +59,9 @@ __global__ void __launch_bounds__(kThreads) aa_dots_kernel(AADots a, size_t n4, 
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
   for (int j = 0; j < 2 * WF_AA_MAX; ++j) {
-    double v = acc[j];
+    float v = acc[j];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) sred[w][j] = v;
+    if (lane == 0) sred[w][j] = (double)v;
   }
   __syncthreads();
   if (threadIdx.x < 2 * WF_AA_MAX) {
@@ -168,7 +172,8 @@ int launch_aa_diff(float* df, float* fprev, const float* e, size_t n, cudaStream
 
 int launch_aa_lsq(const AADots& a, size_t n, double* part, int slot, double* G, float* gamma, cudaStream_t s) {
   const size_t n4 = n / 4;
-  const int g = std::min(grid_for(n4), aa_dots_blocks());
+  // two CTAs per SM: few partials for the one-block solve to sum
+  const int g = std::min(std::max(1, grid_for(n4) / 2), aa_dots_blocks());
   aa_dots_kernel<<<g, kThreads, 0, s>>>(a, n4, part);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return (int)e;
