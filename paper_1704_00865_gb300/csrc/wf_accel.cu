@@ -71,24 +71,26 @@ __global__ void __launch_bounds__(kThreads) aa_dots_kernel(AADots a, size_t n4, 
   }
 }
 
-// The partials of all blocks summed in block order (thread j: dot j), then,
+// The partials of all blocks summed in a fixed order -- warp j sums dot j,
+// lane k the partials of blocks k, k + 32, ..., then a shuffle tree -- and,
 // by one thread, the least-squares step: row and column `slot` of the Gram
 // matrix G = Delta F^T Delta F (held in device memory across corrections)
 // take the new products, and (G + eps diag) gamma = Delta F^T f is solved by
 // Cholesky in FP64.  A column whose pivot falls below 1e-10 of the largest
 // diagonal (dependent on the others to FP32 accuracy) gets gamma = 0.
-__global__ void aa_solve_kernel(const double* part, int nblocks, int slot, int n, double* G, float* gamma) {
+constexpr int kSolveThreads = 2 * WF_AA_MAX * 32;
+__global__ void __launch_bounds__(kSolveThreads) aa_solve_kernel(const double* part, int nblocks, int slot, int n,
+                                                                 double* G, float* gamma) {
   __shared__ double dots[2 * WF_AA_MAX];
-  const int j = threadIdx.x;
-  if (j < 2 * WF_AA_MAX) {
-    double v = 0.0;
-    for (int b = 0; b < nblocks; ++b) v += part[(size_t)b * 2 * WF_AA_MAX + j];
-    dots[j] = v;
-  }
+  __shared__ double L[WF_AA_MAX][WF_AA_MAX];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double v = 0.0;
+  for (int b = lane; b < nblocks; b += 32) v += part[(size_t)b * 2 * WF_AA_MAX + w];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (lane == 0) dots[w] = v;
   __syncthreads();
-  if (j != 0) return;
+  if (threadIdx.x != 0) return;
   for (int k = 0; k < n; ++k) G[slot * WF_AA_MAX + k] = G[k * WF_AA_MAX + slot] = dots[k];
-  double L[WF_AA_MAX][WF_AA_MAX];
   bool use[WF_AA_MAX];
   double g[WF_AA_MAX], y[WF_AA_MAX];
   double dmax = 0.0;
@@ -104,25 +106,25 @@ __global__ void aa_solve_kernel(const double* part, int nblocks, int slot, int n
     use[i] = true;
     L[i][i] = sqrt(d);
     for (int r = i + 1; r < n; ++r) {
-      double v = G[r * WF_AA_MAX + i];
+      double x = G[r * WF_AA_MAX + i];
       for (int k = 0; k < i; ++k)
-        if (use[k]) v -= L[r][k] * L[i][k];
-      L[r][i] = v / L[i][i];
+        if (use[k]) x -= L[r][k] * L[i][k];
+      L[r][i] = x / L[i][i];
     }
   }
   for (int i = 0; i < n; ++i) {
     if (!use[i]) continue;
-    double v = dots[WF_AA_MAX + i];
+    double x = dots[WF_AA_MAX + i];
     for (int k = 0; k < i; ++k)
-      if (use[k]) v -= L[i][k] * y[k];
-    y[i] = v / L[i][i];
+      if (use[k]) x -= L[i][k] * y[k];
+    y[i] = x / L[i][i];
   }
   for (int i = n - 1; i >= 0; --i) {
     if (!use[i]) continue;
-    double v = y[i];
+    double x = y[i];
     for (int k = i + 1; k < n; ++k)
-      if (use[k]) v -= L[k][i] * g[k];
-    g[i] = v / L[i][i];
+      if (use[k]) x -= L[k][i] * g[k];
+    g[i] = x / L[i][i];
   }
   for (int i = 0; i < WF_AA_MAX; ++i) gamma[i] = i < n ? (float)g[i] : 0.f;
 }
@@ -177,7 +179,7 @@ int launch_aa_lsq(const AADots& a, size_t n, double* part, int slot, double* G, 
   aa_dots_kernel<<<g, kThreads, 0, s>>>(a, n4, part);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return (int)e;
-  aa_solve_kernel<<<1, 2 * WF_AA_MAX, 0, s>>>(part, g, slot, a.nb, G, gamma);
+  aa_solve_kernel<<<1, kSolveThreads, 0, s>>>(part, g, slot, a.nb, G, gamma);
   return (int)cudaGetLastError();
 }
 
