@@ -125,19 +125,21 @@ def test_persistent_batch_matches_the_oracle_sweep_for_sweep(wf, shape_choice):
         assert abs(st["rel_rho_u"] - r["rel_u"]) < 2e-3 * r["rel_u"], (p.shape, st, r["rel_u"])
 
 
-def test_persistent_batch_refined_solves_agree_with_single_map_solves(wf):
+@pytest.mark.parametrize("refine,accel", [(2, 0), (4, 3)])
+def test_persistent_batch_refined_solves_agree_with_single_map_solves(wf, refine, accel):
     # the whole solve (first run, corrections with their masked-pixel source,
-    # the refined s) for each map of a mixed batch, against the same solve of
-    # each map alone (lanes = 1, the per-map kernels)
+    # plain or Anderson-combined, the refined s) for each map of a mixed
+    # batch, against the same solve of each map alone (lanes = 1, the per-map
+    # kernels)
     sizes = [512, 256, 1024, 384, 256]
     probs = [synth.make_problem(n, n, 4200 + i, amp_jitter=0.5) for i, n in enumerate(sizes)]
     sched = wf.make_schedule("fixed", [30.0, 3.0], [200, 200])
-    kw = dict(residual_every=20, max_iters=400, refine=2, refine_max_iters=300, refine_lam1_iters=100,
-              refine_tol_scale=1.0, autotune=0)
+    kw = dict(residual_every=20, max_iters=400, refine=refine, refine_max_iters=300, refine_lam1_iters=100,
+              refine_tol_scale=1.0, autotune=0, refine_accel=accel)
     rc, stats, outs = _batch_solve(wf, probs, 0, sched, 0.0, **kw)
     _, stats1, outs1 = _batch_solve(wf, probs, 1, sched, 0.0, **kw)
     for p, a, b, sa, sb in zip(probs, outs, outs1, stats, stats1):
-        assert sa["iters"] == sb["iters"] == 1000, (p.shape, sa, sb)
+        assert sa["iters"] == sb["iters"] == 400 + 300 * refine, (p.shape, sa, sb)
         assert rel(a, b) < 1e-5, (p.shape, rel(a, b))
 
 
