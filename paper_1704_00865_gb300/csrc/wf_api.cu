@@ -96,9 +96,10 @@ struct wf_plan_s {
     long long last_use = 0;
   } chunk[2];
   long long chunk_clock = 0;
-  // an eager chunk has run on this plan, so every kernel's one-time set-up
-  // (attributes, occupancy queries) is done and chunks may be captured
-  bool chunk_warm = false;
+  // keys of the chunks that have run eagerly on this plan: a chunk is
+  // captured only after its kernels have run once outside a capture, so
+  // their one-time set-up (attributes, occupancy queries) is done
+  std::vector<std::vector<unsigned char>> chunk_seen;
   std::vector<void*> allocs;
 };
 
@@ -1116,9 +1117,11 @@ static int wf_run_on(wf_plan_t P, const wf_schedule* sch, double tol, wf_stats* 
   put(&par, 8); put(&src, 8);
   if (P->p.trace) put(&c.run_index, 4);  // stamped into trace records
   const bool use_graph = (per_chunk % 2 == 0);
+  bool seen = false;
+  for (const auto& k : P->chunk_seen) seen = seen || (k == key);
   for (;;) {
     const bool full = enq + per_chunk <= cap;
-    if (use_graph && full && P->chunk_warm) {
+    if (use_graph && full && seen) {
       wf_plan_s::ChunkGraph* G = nullptr;
       for (auto& g : P->chunk)
         if (g.exec && g.key == key) G = &g;
@@ -1155,7 +1158,10 @@ static int wf_run_on(wf_plan_t P, const wf_schedule* sch, double tol, wf_stats* 
       int rc = enqueue_chunk(enq);
       if (rc) return rc;
       enq = std::min(cap, e0 + per_chunk);
-      P->chunk_warm = true;
+      if (!seen) {
+        P->chunk_seen.push_back(key);
+        seen = true;
+      }
     }
     CK(cudaMemcpyAsync(P->h_st, P->st, sizeof(WfState), cudaMemcpyDeviceToHost, P->stream));
     CK(cudaStreamSynchronize(P->stream));
